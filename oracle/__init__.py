@@ -1,0 +1,222 @@
+"""CPU oracle for the 0th persistent homology barcode path -- TEST
+INFRASTRUCTURE ONLY.
+
+A thin ctypes wrapper over ``ph0_oracle.c`` (plain single-threaded C, binary64
+arithmetic, compiled with ``-ffp-contract=off``).  It restates Rawson's barcode
+algorithm (Sec. 2; Sec. 4 steps 1-5) literally: distances, sort, de-duplication
+into D, the vertex-by-edge matrix over F2[t], and a left-to-right column
+reduction of every column with no early exit.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It shares no code with the CUDA library and
+imports nothing from it.
+
+Pins that keep the oracle honest live in ``tests/test_oracle_*.py``; the
+functions here with no such pin are listed there as "parity unpinned" (none at
+present).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ph0_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libph0_oracle.so")
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+           "-shared", "-fPIC"]
+
+_lock = threading.Lock()
+_lib = None
+
+BAR_DTYPE = np.dtype([
+    ("u", np.int32), ("v", np.int32), ("a", np.uint32), ("low", np.int32),
+    ("order", np.int64), ("death_sq", np.float64), ("death", np.float64),
+])
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (host architecture, no native tuning)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+            sig = {
+                "ph0o_edge_endpoints": [i64, vp, vp],
+                "ph0o_distances": [vp, i64, i32, i64, vp],
+                "ph0o_distances_f64": [vp, i64, i32, i64, vp],
+                "ph0o_sort_edges": [vp, vp, vp, i64, vp],
+                "ph0o_dedupe": [vp, i64, vp, vp],
+                "ph0o_reduce": [i64, vp, vp, i64, vp, vp, vp],
+                "ph0o_reduce_dense": [i64, vp, vp, vp, i64, vp, vp, vp],
+                "ph0o_barcodes": [vp, i64, i32, i64, vp, vp, vp, vp],
+                "ph0o_death_gradient": [vp, i64, i32, i64, vp, vp, vp, i64, vp],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def _points(x) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if x.ndim != 2:
+        raise ValueError("points must be [N, d]")
+    return x
+
+
+def n_edges(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def edge_endpoints(n: int):
+    """(u, v) of every edge in lexicographic order (the edge id order)."""
+    m = n_edges(n)
+    u = np.empty(m, np.int32)
+    v = np.empty(m, np.int32)
+    _check(_load().ph0o_edge_endpoints(n, _ptr(u), _ptr(v)), "endpoints")
+    return u, v
+
+
+def distances(x) -> np.ndarray:
+    """Step 1: binary64 squared distance of every edge, in edge id order."""
+    x = _points(x)
+    n, d = x.shape
+    out = np.empty(n_edges(n), np.float64)
+    _check(_load().ph0o_distances(_ptr(x), n, d, d, _ptr(out)), "distances")
+    return out
+
+
+def distances_f64(x) -> np.ndarray:
+    """Squared distances of binary64 points (finite differences)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    n, d = x.shape
+    out = np.empty(n_edges(n), np.float64)
+    _check(_load().ph0o_distances_f64(_ptr(x), n, d, d, _ptr(out)), "distances_f64")
+    return out
+
+
+def sort_edges(d2: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Step 2: edge ids sorted by (squared distance, u, v)."""
+    d2 = np.ascontiguousarray(d2, np.float64)
+    u = np.ascontiguousarray(u, np.int32)
+    v = np.ascontiguousarray(v, np.int32)
+    order = np.empty(len(d2), np.int64)
+    _check(_load().ph0o_sort_edges(_ptr(d2), _ptr(u), _ptr(v), len(d2),
+                                   _ptr(order)), "sort")
+    return order
+
+
+def dedupe(d2_sorted: np.ndarray):
+    """Step 3: a (1-based index into D) per sorted position, and |D|."""
+    d2_sorted = np.ascontiguousarray(d2_sorted, np.float64)
+    a = np.empty(len(d2_sorted), np.uint32)
+    nd = ctypes.c_int64(0)
+    _check(_load().ph0o_dedupe(_ptr(d2_sorted), len(d2_sorted), _ptr(a),
+                               ctypes.byref(nd)), "dedupe")
+    return a, int(nd.value)
+
+
+def reduce(n: int, u_sorted: np.ndarray, v_sorted: np.ndarray):
+    """Steps 4-5 (sparse F2 supports): low per column (-1 = zero column),
+    pivot_of per row (-1 = never a pivot), and the number of column additions."""
+    u_sorted = np.ascontiguousarray(u_sorted, np.int32)
+    v_sorted = np.ascontiguousarray(v_sorted, np.int32)
+    m = len(u_sorted)
+    low = np.empty(m, np.int32)
+    pivot_of = np.empty(n, np.int64)
+    steps = ctypes.c_int64(0)
+    _check(_load().ph0o_reduce(n, _ptr(u_sorted), _ptr(v_sorted), m, _ptr(low),
+                               _ptr(pivot_of), ctypes.byref(steps)), "reduce")
+    return low, pivot_of, int(steps.value)
+
+
+def reduce_dense(n: int, u_sorted, v_sorted, a):
+    """Steps 4-5 on the literal N x E matrix over F2[t] (N <= 64, E <= 4096):
+    low per column, exponent b of each pivot entry t^b, homogeneity flags."""
+    u_sorted = np.ascontiguousarray(u_sorted, np.int32)
+    v_sorted = np.ascontiguousarray(v_sorted, np.int32)
+    a = np.ascontiguousarray(a, np.uint32)
+    m = len(u_sorted)
+    low = np.empty(m, np.int32)
+    b = np.empty(m, np.int32)
+    hom = np.empty(m, np.int32)
+    _check(_load().ph0o_reduce_dense(n, _ptr(u_sorted), _ptr(v_sorted), _ptr(a),
+                                     m, _ptr(low), _ptr(b), _ptr(hom)),
+           "reduce_dense")
+    return low, b, hom
+
+
+def barcodes(x):
+    """Whole path: (bars structured array in filtration order, infinite-bar
+    vertex, |D|)."""
+    x = _points(x)
+    n, d = x.shape
+    bars = np.zeros(max(n - 1, 1), BAR_DTYPE)
+    nb = ctypes.c_int64(0)
+    inf_v = ctypes.c_int32(-1)
+    nd = ctypes.c_int64(0)
+    _check(_load().ph0o_barcodes(_ptr(x), n, d, d, _ptr(bars), ctypes.byref(nb),
+                                 ctypes.byref(inf_v), ctypes.byref(nd)),
+           "barcodes")
+    return bars[: nb.value].copy(), int(inf_v.value), int(nd.value)
+
+
+def death_gradient(x64, bar_u, bar_v, dl_ddeath):
+    """d loss / d points in binary64 for fixed killing edges."""
+    x64 = np.ascontiguousarray(np.asarray(x64, np.float64))
+    n, d = x64.shape
+    bar_u = np.ascontiguousarray(bar_u, np.int32)
+    bar_v = np.ascontiguousarray(bar_v, np.int32)
+    g = np.ascontiguousarray(dl_ddeath, np.float64)
+    out = np.empty((n, d), np.float64)
+    _check(_load().ph0o_death_gradient(_ptr(x64), n, d, d, _ptr(bar_u),
+                                       _ptr(bar_v), _ptr(g), len(bar_u),
+                                       _ptr(out)), "gradient")
+    return out
+
+
+def pipeline(x):
+    """Every intermediate of the path, for step-by-step parity tests:
+    dict with d2 (edge id order), order, sorted u/v/d2, a, |D|, low, bars."""
+    x = _points(x)
+    n = x.shape[0]
+    u, v = edge_endpoints(n)
+    d2 = distances(x)
+    order = sort_edges(d2, u, v)
+    us, vs, d2s = u[order], v[order], d2[order]
+    a, nd = dedupe(d2s)
+    low, pivot_of, steps = reduce(n, us, vs)
+    bars, inf_v, _ = barcodes(x)
+    return dict(u=u, v=v, d2=d2, order=order, u_sorted=us, v_sorted=vs,
+                d2_sorted=d2s, a=a, n_distinct=nd, low=low, pivot_of=pivot_of,
+                steps=steps, bars=bars, inf_vertex=inf_v)
