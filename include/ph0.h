@@ -1,0 +1,161 @@
+/*
+ * ph0.h -- C ABI of the GB300 (sm_103a) 0th persistent homology barcode
+ * library, libph0.so.
+ *
+ * Problem (Rawson, "Linear Run Time of Persistent Homology Computation with
+ * GPU Parallelization", Sec. 2): given N data points X in E^d, compute the
+ * barcodes of the Vietoris-Rips filtration in dimension 0.  Every vertex is
+ * born at 0 (Sec. 1: near epsilon = 0 the complex has a vertex per point and
+ * no edges); an edge that joins two disconnected subgraphs ends one class
+ * (Sec. 1).  The path has the paper's five steps (Sec. 2; Sec. 4 steps 1-5):
+ *   1. the N(N-1)/2 pairwise distances,
+ *   2. a sort of the edges by distance,
+ *   3. de-duplication into D and the 1-based index a of each edge in D,
+ *   4. the vertex-by-edge boundary matrix M over F2[t], M(i,j) = t^a(j),
+ *   5. column reduction of M; each remaining pivot entry t^b is a bar (0, b).
+ *
+ * Conventions fixed here where the paper is silent:
+ *   - distances are computed squared, in binary64 from binary32 inputs, as
+ *     s = 0; for k in 0..d-1: t = x[v,k] - x[u,k]; s = s + t*t, with every
+ *     subtraction, product and sum rounded to nearest-even (no fused
+ *     multiply-add); the distance is sqrt(s), a monotone map, so ties and
+ *     order are those of s;
+ *   - edges with equal distance are ordered by (u, v) lexicographically;
+ *   - the pivot ("low") of a column is its largest row index; then the single
+ *     bar that never dies sits on vertex 0.
+ *
+ * Memory: every pointer named *_dev is CUDA device memory (or managed memory)
+ * owned by the caller; the library allocates nothing and keeps no global
+ * state.  `ws` is a caller-owned device workspace of at least
+ * ph0_workspace_bytes() bytes, 256-byte aligned; one workspace serves one call
+ * in flight at a time.  `stream` is a cudaStream_t passed as void* (NULL =
+ * the legacy default stream).  All compute calls are asynchronous on
+ * `stream`: they return host-detected errors immediately and leave
+ * device-detected errors (non-finite input, a bounded wait that timed out) in
+ * the workspace, where ph0_finish() reads them.
+ *
+ * Limits: 1 <= N <= 65535 (vertex ids are packed into 16 bits, so E < 2^31),
+ * 1 <= d <= 1024.
+ */
+#ifndef PH0_H
+#define PH0_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PH0_OK = 0,
+    PH0_EINVAL = 1,      /* bad argument: n < 1, d < 1, ld < d, null or misaligned pointer */
+    PH0_ENONFINITE = 2,  /* a coordinate is NaN or +-Inf (detected on the device) */
+    PH0_ETOOBIG = 3,     /* n > 65535 or d > 1024 */
+    PH0_ENOMEM = 4,      /* workspace smaller than ph0_workspace_bytes() */
+    PH0_ETIMEOUT = 5,    /* a bounded device-side wait gave up (the kernel returned cleanly) */
+    PH0_ECUDA = 6,       /* a CUDA runtime call failed */
+    PH0_EBUSY = 7,       /* the resource is in use */
+    PH0_EINTERNAL = 8    /* an internal consistency check failed */
+} ph0_status;
+
+/* One finite bar (birth 0).  40 bytes, naturally aligned. */
+typedef struct {
+    int32_t u, v;      /* killing edge, u < v                                   */
+    uint32_t a;        /* 1-based index of its squared distance in D (the b of t^b) */
+    int32_t low;       /* pivot row of its reduced column: the vertex whose class
+                          this edge ends (max of the two component minima)       */
+    int64_t order;     /* 0-based position of the edge in the sorted edge list  */
+    double death_sq;   /* binary64 squared distance of the edge                 */
+    double death;      /* sqrt(death_sq), IEEE round to nearest                 */
+} ph0_bar;
+
+/* Counters of the last call on a workspace, read back by ph0_finish(). */
+typedef struct {
+    int32_t status;          /* ph0_status of the device-side work            */
+    int32_t sort_passes;     /* radix passes that moved data                  */
+    int32_t key_bits;        /* varying key bits sorted                       */
+    int32_t windows;         /* reduction windows processed                   */
+    int64_t n_distinct;      /* |D|                                           */
+    int64_t edges_scanned;   /* sorted edges examined before the early exit   */
+    int64_t candidates;      /* edges that reached the pivot-claiming rounds  */
+    int64_t rounds;          /* pivot-claiming rounds over all windows        */
+    int64_t n_bars;          /* finite bars written                           */
+} ph0_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char *ph0_strerror(int status);
+
+/* Library ABI version (incremented on any incompatible change). */
+int32_t ph0_abi_version(void);
+
+/* Bytes of workspace ph0_barcodes() and the step entry points need for a
+ * cloud of n points in dimension d (0 on invalid sizes). */
+size_t ph0_workspace_bytes(int64_t n, int32_t d);
+
+/* Whole path, steps 1-5 (Sec. 2; Sec. 4 steps 1-5).
+ *   pts_dev   float32 [n, ld] row-major, the first d columns are used
+ *   bars_dev  ph0_bar [n-1] output, in filtration order (increasing `order`)
+ * The bar that never dies is (0, +inf) on vertex 0 and is not written.
+ * Asynchronous; call ph0_finish() for the device status. */
+int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                 ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Waits for `stream`, then returns the device status of the last call made
+ * with `ws` and, when stats != NULL, its counters. */
+int ph0_finish(const void *ws, void *stream, ph0_stats *stats);
+
+/* ---- step entry points (each one step of the path, for testing and reuse) ---- */
+
+/* Step 1 (Sec. 2 "calculate the distance between every pair of points";
+ * Sec. 4 step 1).  Writes, for every edge u<v at index
+ * e = u*(2n-u-1)/2 + (v-u-1) (lexicographic order):
+ *   key_dev[e] = bit pattern of the binary64 squared distance (uint64),
+ *   val_dev[e] = (u << 16) | v.
+ * key_dev: uint64 [E], val_dev: uint32 [E], E = n(n-1)/2, 16-byte aligned. */
+int ph0_distances(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                  uint64_t *key_dev, uint32_t *val_dev,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Step 2 (Sec. 2 "sort it in increasing order"; Sec. 4 step 2).  Stable sort
+ * of the m (key, val) pairs by key, in place; keys are binary64 bit patterns
+ * of non-negative numbers (unsigned order = numeric order).  Input in val
+ * order gives the total order (distance, u, v).  m <= 2^31 - 1; `ws` must be
+ * sized for some n with n(n-1)/2 >= m. */
+int ph0_sort(uint64_t *key_dev, uint32_t *val_dev, int64_t m,
+             void *ws, size_t ws_bytes, void *stream);
+
+/* Step 3 (Sec. 2 "Remove duplicate elements in E and call it D ... a is the
+ * index of edge j in D which ranges from 1 to the length of D").
+ *   key_sorted_dev  uint64 [m] sorted keys;  a_dev  uint32 [m] output. */
+int ph0_dedupe(const uint64_t *key_sorted_dev, int64_t m, uint32_t *a_dev,
+               void *ws, size_t ws_bytes, void *stream);
+
+/* Steps 4-5 (Sec. 2 "build a matrix M ... column reduce this matrix"; Sec. 4
+ * steps 3-5).  Column p of M has the rows u_p, v_p of val_sorted_dev[p], both
+ * t^a[p]; it is never materialised.  The columns are reduced in order with a
+ * pivot table claimed by atomic priority (lower filtration position wins,
+ * the loser retries), stopping once n-1 pivots exist.  Writes the n-1 bars
+ * in filtration order.  Inputs: sorted val (uint32 [m]), a (uint32 [m]),
+ * sorted key (uint64 [m]); m = n(n-1)/2. */
+int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
+               const uint32_t *a_dev, const uint64_t *key_sorted_dev,
+               ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- differentiation ---- */
+
+/* Backward of death_i = |x_v - x_u| for fixed killing edges:
+ *   grad[u] += g_i (x_u - x_v) / death_i,  grad[v] -= the same,
+ * g_i = dl_ddeath_dev[i], in binary64, cast to float32 once at the end; a bar
+ * of length 0 contributes 0.  grad_dev float32 [n, d] (dense, row-major) is
+ * overwritten.  `ws` as for ph0_barcodes with the same n, d. */
+int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d,
+                          int64_t ld, const ph0_bar *bars_dev, int64_t n_bars,
+                          const double *dl_ddeath_dev, float *grad_dev,
+                          void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PH0_H */

@@ -1,0 +1,106 @@
+"""ctypes binding of libph0.so (the C ABI in include/ph0.h).
+
+Argument marshalling only: every step of the barcode path runs in the CUDA
+kernels of the library.  Torch tensors serve as device buffers and torch's
+current stream is passed through.  If the library is missing the binding
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libph0.so")
+
+BAR_DTYPE = np.dtype([
+    ("u", np.int32), ("v", np.int32), ("a", np.uint32), ("low", np.int32),
+    ("order", np.int64), ("death_sq", np.float64), ("death", np.float64),
+])
+BAR_BYTES = BAR_DTYPE.itemsize  # 40
+
+STATUS = {
+    0: "PH0_OK", 1: "PH0_EINVAL", 2: "PH0_ENONFINITE", 3: "PH0_ETOOBIG",
+    4: "PH0_ENOMEM", 5: "PH0_ETIMEOUT", 6: "PH0_ECUDA", 7: "PH0_EBUSY",
+    8: "PH0_EINTERNAL",
+}
+
+
+class Ph0Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
+        ("key_bits", ctypes.c_int32), ("windows", ctypes.c_int32),
+        ("n_distinct", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
+        ("candidates", ctypes.c_int64), ("rounds", ctypes.c_int64),
+        ("n_bars", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_I64, _I32, _VP, _SZ = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
+
+# name -> (restype, argtypes); the same names as include/ph0.h
+SIGNATURES = {
+    "ph0_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ph0_abi_version": (ctypes.c_int32, []),
+    "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
+    "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
+    "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
+    "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
+    "ph0_sort": (ctypes.c_int, [_VP, _VP, _I64, _VP, _SZ, _VP]),
+    "ph0_dedupe": (ctypes.c_int, [_VP, _I64, _VP, _VP, _SZ, _VP]),
+    "ph0_reduce": (ctypes.c_int, [_I64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "ph0_barcodes_backward": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _I64, _VP, _VP,
+                                             _VP, _SZ, _VP]),
+}
+
+
+def load(path: str | None = None):
+    """Load libph0.so (fails loudly if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"libph0.so not found at {p}: build it with "
+                "`python -m paper_2203_02527_gb300.build` (there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().ph0_strerror(code).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "?"
+
+
+def check(code: int, what: str):
+    if code != 0:
+        raise Ph0Error(code, what)
+
+
+def workspace_bytes(n: int, d: int) -> int:
+    return int(load().ph0_workspace_bytes(n, d))

@@ -1,0 +1,273 @@
+// ph0_capi.cu -- the C ABI of libph0 (declared in include/ph0.h): argument
+// checks, workspace carving and kernel launches for the five steps of the
+// barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).  No allocation, no global
+// state: every buffer is caller-owned and every call is asynchronous on the
+// caller's stream.
+#include <cstring>
+
+#include "ph0_common.cuh"
+
+namespace ph0 {
+
+cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
+                        uint32_t *val, Header *h, cudaStream_t s);
+cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s);
+cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
+cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
+                               cudaStream_t s);
+cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
+                               const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
+cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
+                          int64_t m, uint32_t *a, uint64_t *look, Header *h, cudaStream_t s);
+cudaError_t launch_backward(const float *pts, int64_t n, int32_t d, int64_t ld, const ph0_bar *bars,
+                            int64_t nb, const double *dl, float *grad, double *acc, cudaStream_t s);
+
+cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s);
+cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
+                        const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
+                        const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
+                        const uint64_t *key1, const Header *sort_h, const uint32_t *a,
+                        ph0_bar *bars, cudaStream_t s);
+
+namespace {
+
+int check_sizes(int64_t n, int32_t d, int64_t ld) {
+    if (n < 1 || d < 1 || ld < d) return PH0_EINVAL;
+    if (n > kMaxN || d > kMaxD) return PH0_ETOOBIG;
+    return PH0_OK;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Smallest n whose edge count covers m.
+int64_t n_for_edges(int64_t m) {
+    int64_t n = 2;
+    while (n_edges(n) < m) ++n;
+    return n;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PH0_OK : PH0_ECUDA; }
+
+// Zero the header and prepare the main sort (first look-back buffer).
+cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s) {
+    Header *h = at<Header>(ws, L.hdr);
+    cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
+    if (e != cudaSuccess) return e;
+    return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s);
+}
+
+// Steps 4-5 plus the read-out: reduce, order the pivot columns by position,
+// emit the bars.  val/key/a are either the workspace's ping-pong buffers
+// (sort_h != null selects the one holding the sorted data) or the caller's.
+cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
+                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
+                            const Header *sort_h, const uint32_t *a, ph0_bar *bars, cudaStream_t s) {
+    Header *h = at<Header>(ws, L.hdr);
+    const int64_t m = n_edges(n);
+    ReduceArgs A;
+    A.n = n;
+    A.m = m;
+    A.val0 = val0;
+    A.val1 = val1;
+    A.sort_h = sort_h;
+    A.comp = at<uint32_t>(ws, L.comp);
+    A.parent = at<uint32_t>(ws, L.parent);
+    A.res = at<unsigned long long>(ws, L.res);
+    A.cand0 = at<uint32_t>(ws, L.cand[0]);
+    A.cand1 = at<uint32_t>(ws, L.cand[1]);
+    A.candr = at<uint32_t>(ws, L.candr);
+    A.kill_key = at<unsigned long long>(ws, L.kill_key[0]);
+    A.kill_val = at<uint32_t>(ws, L.kill_val[0]);
+    A.h = h;
+    int64_t w0 = 2 * n > 4096 ? 2 * n : 4096;
+    A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
+    cudaError_t e = launch_reduce(A, s);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = n - 1;
+    if (nb <= 0) return cudaSuccess;
+    // order the n-1 pivot columns by sorted position (their discovery order
+    // within a window is not the filtration order)
+    Header *kh = at<Header>(ws, L.aux_hdr);
+    e = cudaMemsetAsync(kh, 0, kHeaderBytes, s);
+    if (e != cudaSuccess) return e;
+    const int64_t ktiles = (nb + kSortTile - 1) / kSortTile;
+    e = launch_sort_init(kh, at<uint64_t>(ws, L.kill_look[0]), ktiles, s);
+    if (e != cudaSuccess) return e;
+    uint64_t *kk0 = at<uint64_t>(ws, L.kill_key[0]), *kk1 = at<uint64_t>(ws, L.kill_key[1]);
+    uint32_t *kv0 = at<uint32_t>(ws, L.kill_val[0]), *kv1 = at<uint32_t>(ws, L.kill_val[1]);
+    e = launch_keystats(kk0, nb, kh, s);
+    if (e != cudaSuccess) return e;
+    e = launch_sort_passes(kk0, kk1, kv0, kv1, nb, at<uint64_t>(ws, L.kill_look[0]),
+                           at<uint64_t>(ws, L.kill_look[1]), kh, s);
+    if (e != cudaSuccess) return e;
+    return launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
+                       reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
+                       key0, key1, sort_h, a, bars, s);
+}
+
+}  // namespace
+}  // namespace ph0
+
+using namespace ph0;
+
+extern "C" {
+
+const char *ph0_strerror(int status) {
+    switch (status) {
+        case PH0_OK: return "ok";
+        case PH0_EINVAL: return "invalid argument";
+        case PH0_ENONFINITE: return "non-finite coordinate";
+        case PH0_ETOOBIG: return "size above the supported maximum (n <= 65535, d <= 1024)";
+        case PH0_ENOMEM: return "workspace too small";
+        case PH0_ETIMEOUT: return "a bounded device-side wait timed out";
+        case PH0_ECUDA: return "CUDA runtime error";
+        case PH0_EBUSY: return "busy";
+        case PH0_EINTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int32_t ph0_abi_version(void) { return 1; }
+
+size_t ph0_workspace_bytes(int64_t n, int32_t d) {
+    if (check_sizes(n, d, d) != PH0_OK) return 0;
+    return Layout(n, d).total;
+}
+
+int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                 void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint32_t *a = at<uint32_t>(ws, L.a);
+    cudaError_t e = begin_call(ws, L, s);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
+    if (e == cudaSuccess)
+        e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
+                               at<uint64_t>(ws, L.look[1]), h, s);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s);
+    return cuda_status(e);
+}
+
+int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
+    if (!ws) return PH0_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    Header hh;
+    e = cudaMemcpy(&hh, ws, sizeof(Header), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    if (stats) {
+        stats->status = hh.status;
+        stats->sort_passes = hh.sort_passes;
+        stats->key_bits = hh.key_bits;
+        stats->windows = hh.windows;
+        stats->n_distinct = hh.n_distinct;
+        stats->edges_scanned = hh.edges_scanned;
+        stats->candidates = hh.candidates;
+        stats->rounds = hh.rounds;
+        stats->n_bars = hh.n_bars;
+    }
+    return hh.status;
+}
+
+int ph0_distances(const float *pts_dev, int64_t n, int32_t d, int64_t ld, uint64_t *key_dev,
+                  uint32_t *val_dev, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (!pts_dev || !ws || (n > 1 && (!key_dev || !val_dev))) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(key_dev, 8) || !aligned(val_dev, 4)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = begin_call(ws, L, s);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, key_dev, val_dev, at<Header>(ws, L.hdr), s);
+    return cuda_status(e);
+}
+
+int ph0_sort(uint64_t *key_dev, uint32_t *val_dev, int64_t m, void *ws, size_t ws_bytes,
+             void *stream) {
+    if (m < 0 || m > int64_t(0x7fffffff)) return PH0_EINVAL;
+    if (m == 0) return PH0_OK;
+    if (!key_dev || !val_dev || !ws) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(key_dev, 8) || !aligned(val_dev, 4)) return PH0_EINVAL;
+    const int64_t n = n_for_edges(m);
+    if (n > kMaxN) return PH0_ETOOBIG;
+    const Layout L(n, 1);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v1 = at<uint32_t>(ws, L.val[1]);
+    const int64_t tiles = (m + kSortTile - 1) / kSortTile;
+    cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
+    if (e == cudaSuccess) e = launch_sort_init(h, at<uint64_t>(ws, L.look[0]), tiles, s);
+    if (e == cudaSuccess) e = launch_keystats(key_dev, m, h, s);
+    if (e == cudaSuccess)
+        e = launch_sort_passes(key_dev, k1, val_dev, v1, m, at<uint64_t>(ws, L.look[0]),
+                               at<uint64_t>(ws, L.look[1]), h, s);
+    if (e == cudaSuccess) e = launch_copy_if_odd(key_dev, k1, val_dev, v1, m, h, s);
+    return cuda_status(e);
+}
+
+int ph0_dedupe(const uint64_t *key_sorted_dev, int64_t m, uint32_t *a_dev, void *ws,
+               size_t ws_bytes, void *stream) {
+    if (m < 0 || m > int64_t(0x7fffffff)) return PH0_EINVAL;
+    if (!ws || (m > 0 && (!key_sorted_dev || !a_dev))) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(key_sorted_dev, 8) || !aligned(a_dev, 4)) return PH0_EINVAL;
+    const int64_t n = m > 0 ? n_for_edges(m) : 2;
+    if (n > kMaxN) return PH0_ETOOBIG;
+    const Layout L(n, 1);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = at<Header>(ws, L.hdr);
+    cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
+    if (e == cudaSuccess)
+        e = launch_dedupe(key_sorted_dev, key_sorted_dev, nullptr, m, a_dev, at<uint64_t>(ws, L.dlook), h, s);
+    return cuda_status(e);
+}
+
+int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev, const uint32_t *a_dev,
+               const uint64_t *key_sorted_dev, ph0_bar *bars_dev, void *ws, size_t ws_bytes,
+               void *stream) {
+    int rc = check_sizes(n, 1, 1);
+    if (rc != PH0_OK) return rc;
+    if (!ws || (n > 1 && (!val_sorted_dev || !a_dev || !key_sorted_dev || !bars_dev)))
+        return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, 1);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(at<Header>(ws, L.hdr), 0, kHeaderBytes, s);
+    if (e == cudaSuccess)
+        e = reduce_and_emit(ws, L, n, val_sorted_dev, val_sorted_dev, key_sorted_dev, key_sorted_dev,
+                            nullptr, a_dev, bars_dev, s);
+    return cuda_status(e);
+}
+
+int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                          const ph0_bar *bars_dev, int64_t n_bars, const double *dl_ddeath_dev,
+                          float *grad_dev, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (n_bars < 0 || n_bars > n - 1) return PH0_EINVAL;
+    if (!pts_dev || !grad_dev || !ws || (n_bars > 0 && (!bars_dev || !dl_ddeath_dev)))
+        return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(bars_dev, 8) || !aligned(dl_ddeath_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return cuda_status(launch_backward(pts_dev, n, d, ld, bars_dev, n_bars, dl_ddeath_dev, grad_dev,
+                                       at<double>(ws, L.grad), s));
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// ph0_common.cuh -- shared device-side definitions of libph0 (sm_103a).
+//
+// Workspace layout, the device status word, bounded waits and small helpers
+// used by the kernels of the barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ph0.h"
+
+namespace ph0 {
+
+// ---------------------------------------------------------------- limits ---
+constexpr int64_t kMaxN = 65535;   // vertex ids packed in 16 bits: E < 2^31
+constexpr int32_t kMaxD = 1024;
+constexpr int kMaxPasses = 8;      // 64-bit keys, digits of at most 8 bits
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Bounded device-side waits: about a second at most, then the kernel records
+// PH0_ETIMEOUT in the status word and returns cleanly.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Radix sort tile: kSortThreads threads x kSortItems keys.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Look-back status word: [63:62] flag, [61:0] count.
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kFlagMask = 3ull << 62;
+constexpr uint64_t kCountMask = ~kFlagMask;
+
+// --------------------------------------------------------------- header ---
+// Lives at offset 0 of the workspace.  Every counter the kernels share.
+struct Header {
+    int32_t status;              // ph0_status, first device error wins
+    int32_t sort_passes;
+    int32_t key_bits;
+    int32_t windows;
+    uint64_t kmin;               // min / max key over the keys being sorted
+    uint64_t kmax;
+    int64_t n_distinct;
+    int64_t edges_scanned;
+    int64_t candidates;
+    int64_t rounds;
+    int64_t n_bars;
+    uint32_t tile_counter[kMaxPasses + 4];
+    // grid barrier of the persistent reduction kernel
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    int32_t abort;
+    uint32_t npiv;               // pivots claimed so far
+    uint32_t nlist[2];           // candidate list lengths (ping-pong)
+    uint32_t pad[6];
+    uint32_t hist[kMaxPasses][kRadix];  // digit histogram per radix pass
+};
+
+constexpr size_t kHeaderBytes = 16384;
+static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) {
+    return (x + a - 1) / a * a;
+}
+
+__host__ __device__ inline int64_t n_edges(int64_t n) { return n * (n - 1) / 2; }
+
+// Candidate list capacity of one reduction window (edges per window).
+constexpr int64_t kMaxWindow = int64_t(1) << 22;
+
+// Byte offsets of every region of the workspace for a cloud of n points in
+// dimension d.  Everything is caller-owned device memory; nothing is
+// allocated by the library.
+struct Layout {
+    int64_t n, m, tiles, ktiles;
+    size_t hdr, aux_hdr;                 // main header, header of the small sorts
+    size_t key[2], val[2], a, look[2];   // edge records, ping-pong, look-back words
+    size_t dlook;                        // look-back words of the de-duplication scan
+    size_t comp, parent, res, cand[2], candr;
+    size_t kill_key[2], kill_val[2], kill_look[2];
+    size_t grad;                         // binary64 gradient accumulator [n, d]
+    size_t total;
+
+    __host__ __device__ Layout(int64_t n_, int32_t d_) : n(n_) {
+        m = n_edges(n);
+        tiles = (m + kSortTile - 1) / kSortTile;
+        ktiles = (n + kSortTile - 1) / kSortTile;
+        int64_t wcap = m < kMaxWindow ? m : kMaxWindow;
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            size_t o = off;
+            off = align_up(off + bytes, 256);
+            return o;
+        };
+        hdr = take(kHeaderBytes);
+        aux_hdr = take(kHeaderBytes);
+        key[0] = take(8 * size_t(m));
+        key[1] = take(8 * size_t(m));
+        val[0] = take(4 * size_t(m));
+        val[1] = take(4 * size_t(m));
+        a = take(4 * size_t(m));
+        look[0] = take(8 * size_t(tiles) * kRadix);
+        look[1] = take(8 * size_t(tiles) * kRadix);
+        dlook = take(8 * size_t(tiles + 1));
+        comp = take(4 * size_t(n));
+        parent = take(4 * size_t(n));
+        res = take(8 * size_t(n));
+        cand[0] = take(4 * size_t(wcap + 1));
+        cand[1] = take(4 * size_t(wcap + 1));
+        candr = take(4 * size_t(wcap + 1));
+        kill_key[0] = take(8 * size_t(n));
+        kill_key[1] = take(8 * size_t(n));
+        kill_val[0] = take(4 * size_t(n));
+        kill_val[1] = take(4 * size_t(n));
+        kill_look[0] = take(8 * size_t(ktiles) * kRadix);
+        kill_look[1] = take(8 * size_t(ktiles) * kRadix);
+        grad = take(8 * size_t(n) * size_t(d_ > 0 ? d_ : 1));
+        total = off;
+    }
+};
+
+// Arguments of the persistent reduction kernel (steps 4-5).
+struct ReduceArgs {
+    int64_t n, m;
+    const uint32_t *val0, *val1;   // sorted edge records (buffer chosen by the sort plan)
+    const Header *sort_h;          // header of the sort (plan), or null: use val0
+    uint32_t *comp;                // [n] root of each vertex at the window start
+    uint32_t *parent;              // [n] link of each root claimed in this window
+    unsigned long long *res;       // [n] claim of each root: (~round << 32) | position
+    uint32_t *cand0, *cand1;       // candidate lists (ping-pong)
+    uint32_t *candr;               // [list] roots of each candidate in this round
+    unsigned long long *kill_key;  // [n] position of each pivot column
+    uint32_t *kill_val;            // [n] its pivot row
+    Header *h;
+    int64_t w0;                    // first window size
+};
+
+template <typename T>
+__host__ __device__ inline T *at(void *ws, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+// ------------------------------------------------------------ device util ---
+__device__ __forceinline__ void set_status(Header *h, int code) {
+    atomicCAS(&h->status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+__device__ __forceinline__ int32_t ld_volatile(const int32_t *p) {
+    return *reinterpret_cast<const volatile int32_t *>(p);
+}
+__device__ __forceinline__ void st_volatile(uint64_t *p, uint64_t v) {
+    *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+
+// Edge index of (u, v), u < v, in lexicographic order.
+__host__ __device__ __forceinline__ int64_t edge_index(int64_t n, int64_t u, int64_t v) {
+    return u * (2 * n - u - 1) / 2 + (v - u - 1);
+}
+
+// Radix plan.  Pass 0 sorts the raw low 8 bits (its histogram is taken where
+// the keys are produced, before kmin is known); the other passes sort 8-bit
+// digits of (key - kbase), kbase = kmin with its low 8 bits cleared, which
+// leaves the low digit unchanged and drops the constant high bits.
+struct Plan {
+    uint64_t kbase;
+    int nbits, passes;
+};
+__device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax) {
+    Plan p;
+    p.kbase = kmin & ~uint64_t(kRadix - 1);
+    uint64_t span = kmax > p.kbase ? kmax - p.kbase : 0;
+    p.nbits = span ? 64 - __clzll((long long)span) : 0;
+    p.passes = p.nbits <= kRadixBits ? 1 : 1 + (p.nbits - kRadixBits + kRadixBits - 1) / kRadixBits;
+    return p;
+}
+__device__ __forceinline__ uint32_t digit_of(uint64_t key, const Plan &p, int pass) {
+    if (pass == 0) return uint32_t(key) & (kRadix - 1);
+    return uint32_t((key - p.kbase) >> (kRadixBits * pass)) & (kRadix - 1);
+}
+
+}  // namespace ph0

@@ -1,0 +1,182 @@
+"""Torch-facing wrappers of the C ABI: device buffers and the current stream
+come from PyTorch; all computation is in libph0's CUDA kernels.
+
+    bars = barcodes(points)          # points: float32 [N, d] CUDA tensor
+    bars.death, bars.u, bars.v ...   # CUDA tensors, filtration order
+    bars.numpy()                     # structured array (host copy)
+
+The bar that never dies is (0, +inf) on vertex 0 (not stored).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import BAR_BYTES, BAR_DTYPE, Stats, check
+
+_FIELDS = {  # name -> (byte offset, byte size, torch dtype) in the 40-byte ph0_bar
+    "u": (0, 4, torch.int32), "v": (4, 4, torch.int32), "a": (8, 4, torch.int32),
+    "low": (12, 4, torch.int32), "order": (16, 8, torch.int64),
+    "death_sq": (24, 8, torch.float64), "death": (32, 8, torch.float64),
+}
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() else None)
+
+
+class Workspace:
+    """Caller-owned device workspace for clouds up to (n, d)."""
+
+    def __init__(self, n: int, d: int, device=None):
+        nbytes = _lib.workspace_bytes(n, d)
+        if nbytes == 0:
+            raise _lib.Ph0Error(3, f"workspace_bytes(n={n}, d={d})")
+        self.n, self.d, self.nbytes = n, d, nbytes
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+    @property
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+    def fits(self, n: int, d: int) -> bool:
+        return _lib.workspace_bytes(n, d) <= self.nbytes
+
+
+_ws_cache: dict = {}
+
+
+def _workspace(n: int, d: int, device) -> Workspace:
+    key = (device.index if device.index is not None else torch.cuda.current_device())
+    ws = _ws_cache.get(key)
+    if ws is None or not ws.fits(n, d):
+        ws = Workspace(n, d, device)
+        _ws_cache[key] = ws
+    return ws
+
+
+@dataclass
+class Bars:
+    raw: torch.Tensor          # uint8 [n-1, 40] device buffer
+    n: int
+    stats: dict | None = None
+
+    def __getattr__(self, name):
+        if name in _FIELDS:
+            off, size, dt = _FIELDS[name]
+            nb = self.raw.shape[0]
+            return self.raw[:, off:off + size].contiguous().view(dt).reshape(nb)
+        raise AttributeError(name)
+
+    def numpy(self) -> np.ndarray:
+        return self.raw.cpu().numpy().reshape(-1).view(BAR_DTYPE).copy()
+
+    inf_vertex = 0
+
+
+def _points(pts: torch.Tensor):
+    if not isinstance(pts, torch.Tensor) or not pts.is_cuda:
+        raise TypeError("points must be a CUDA tensor (there is no CPU path)")
+    if pts.dtype != torch.float32 or pts.dim() != 2:
+        raise TypeError("points must be float32 [N, d]")
+    if pts.stride(1) != 1:
+        pts = pts.contiguous()
+    return pts, pts.shape[0], pts.shape[1], pts.stride(0)
+
+
+def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False,
+             sync: bool = True) -> Bars:
+    """Finite bars of the 0th persistent homology of the point cloud (steps 1-5)."""
+    pts, n, d, ld = _points(pts)
+    ws = ws or _workspace(n, d, pts.device)
+    bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
+    s = _stream()
+    lib = _lib.load()
+    check(lib.ph0_barcodes(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, s), "ph0_barcodes")
+    st = None
+    if sync or stats:
+        st = finish(ws)
+    return Bars(bars, n, st)
+
+
+def finish(ws: Workspace) -> dict:
+    st = Stats()
+    rc = _lib.load().ph0_finish(ws.ptr, _stream(), ctypes.byref(st))
+    check(rc, "device status")
+    return st.as_dict()
+
+
+# ---------------------------------------------------------------- steps ---
+
+def distances(pts: torch.Tensor, ws: Workspace | None = None):
+    """Step 1: (key int64 [E] = binary64 bits of d2, val int32 [E] = u<<16|v),
+    edges in lexicographic (u, v) order."""
+    pts, n, d, ld = _points(pts)
+    ws = ws or _workspace(n, d, pts.device)
+    m = n * (n - 1) // 2
+    key = torch.empty(m, dtype=torch.int64, device=pts.device)
+    val = torch.empty(m, dtype=torch.int32, device=pts.device)
+    check(_lib.load().ph0_distances(_ptr(pts), n, d, ld, _ptr(key), _ptr(val), ws.ptr, ws.nbytes,
+                                    _stream()), "ph0_distances")
+    finish(ws)
+    return key, val
+
+
+def sort_pairs(key: torch.Tensor, val: torch.Tensor, ws: Workspace | None = None):
+    """Step 2: stable sort of (key, val) by key (unsigned), in place."""
+    m = key.numel()
+    assert key.dtype == torch.int64 and val.dtype == torch.int32 and val.numel() == m
+    n = 2
+    while n * (n - 1) // 2 < m:
+        n += 1
+    ws = ws or _workspace(n, 1, key.device)
+    check(_lib.load().ph0_sort(_ptr(key), _ptr(val), m, ws.ptr, ws.nbytes, _stream()), "ph0_sort")
+    finish(ws)
+    return key, val
+
+
+def dedupe(key_sorted: torch.Tensor, ws: Workspace | None = None):
+    """Step 3: a (int32 [m], 1-based index in D) of sorted keys, and |D|."""
+    m = key_sorted.numel()
+    n = 2
+    while n * (n - 1) // 2 < m:
+        n += 1
+    ws = ws or _workspace(n, 1, key_sorted.device)
+    a = torch.empty(m, dtype=torch.int32, device=key_sorted.device)
+    check(_lib.load().ph0_dedupe(_ptr(key_sorted), m, _ptr(a), ws.ptr, ws.nbytes, _stream()),
+          "ph0_dedupe")
+    st = finish(ws)
+    return a, st["n_distinct"]
+
+
+def reduce(n: int, val_sorted: torch.Tensor, a: torch.Tensor, key_sorted: torch.Tensor,
+           ws: Workspace | None = None) -> Bars:
+    """Steps 4-5 on sorted edges: the n-1 bars."""
+    ws = ws or _workspace(n, 1, val_sorted.device)
+    bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=val_sorted.device)
+    check(_lib.load().ph0_reduce(n, _ptr(val_sorted), _ptr(a), _ptr(key_sorted), _ptr(bars),
+                                 ws.ptr, ws.nbytes, _stream()), "ph0_reduce")
+    return Bars(bars, n, finish(ws))
+
+
+def backward(pts: torch.Tensor, bars: Bars, dl_ddeath: torch.Tensor,
+             ws: Workspace | None = None) -> torch.Tensor:
+    """d loss / d points for fixed killing edges (float32 [N, d])."""
+    pts, n, d, ld = _points(pts)
+    ws = ws or _workspace(n, d, pts.device)
+    g = dl_ddeath.to(dtype=torch.float64).contiguous()
+    grad = torch.empty((n, d), dtype=torch.float32, device=pts.device)
+    nb = bars.raw.shape[0]
+    check(_lib.load().ph0_barcodes_backward(_ptr(pts), n, d, ld, _ptr(bars.raw), nb, _ptr(g),
+                                            _ptr(grad), ws.ptr, ws.nbytes, _stream()),
+          "ph0_barcodes_backward")
+    return grad

@@ -1,0 +1,46 @@
+"""The C ABI library loads and exports every function include/ph0.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ph0.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(ph0_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("ph0_barcodes", "ph0_workspace_bytes", "ph0_finish", "ph0_distances",
+                 "ph0_sort", "ph0_dedupe", "ph0_reduce", "ph0_barcodes_backward",
+                 "ph0_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2203_02527_gb300 import build, _lib
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # host-only calls work without a device
+    lib2 = _lib.load()
+    assert lib2.ph0_abi_version() == 1
+    assert lib2.ph0_strerror(0) == b"ok"
+    assert lib2.ph0_workspace_bytes(0, 3) == 0
+    assert lib2.ph0_workspace_bytes(256, 3) > 256 * 255 // 2 * 12
+    # every binding name is a declared name
+    assert set(_lib.SIGNATURES) <= set(declared_functions())
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    from paper_2203_02527_gb300 import _lib
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "missing.so"))

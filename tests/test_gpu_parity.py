@@ -1,0 +1,171 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: every
+step, element by element, bit-exact (integer, index and binary64 results are
+all exact by construction, so the tolerance is zero)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02527_gb300 import inputs
+from tests import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ph0():
+    from paper_2203_02527_gb300 import ph0
+    return ph0
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def assert_bars_equal(got: np.ndarray, want: np.ndarray):
+    assert len(got) == len(want)
+    for f in ("u", "v", "a", "low", "order"):
+        np.testing.assert_array_equal(got[f], want[f], err_msg=f)
+    for f in ("death_sq", "death"):
+        np.testing.assert_array_equal(got[f].view(np.uint64), want[f].view(np.uint64), err_msg=f)
+
+
+CASES = {
+    "uniform256": lambda: inputs.config_points("uniform256"),
+    "uniform_ragged1000": lambda: inputs.uniform(1000, 3, seed=31),
+    "mixture_ragged777_d8": lambda: inputs.gaussian_mixture(777, 8, k=5, sigma=0.2, seed=32),
+    "circles_small_d16": lambda: inputs.noisy_circles(300, 4, 16, seed=33),
+    "lattice_ties": lambda: inputs.lattice(12, 2),
+    "lattice3d_ties": lambda: inputs.lattice(7, 3),
+    "duplicates": lambda: inputs.with_duplicates(400, 3, 37, seed=34),
+    "exponent_gaps": lambda: inputs.exponent_gaps(300, 5, seed=35),
+    "negative_zero": lambda: inputs.negative_zero_mix(200, 3, seed=36),
+    "simplex": lambda: np.eye(64, dtype=np.float32),
+    "uniform_d1": lambda: inputs.uniform(500, 1, seed=37),
+    "uniform_d33": lambda: inputs.uniform(300, 33, seed=38),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_steps_bit_exact(case):
+    ph0 = _ph0()
+    x = CASES[case]()
+    n = len(x)
+    ref = oracle.pipeline(x)
+    pts = _cuda(x)
+    # step 1
+    key, val = ph0.distances(pts)
+    np.testing.assert_array_equal(_u64(key), ref["d2"].view(np.uint64))
+    want_val = (ref["u"].astype(np.uint32) << 16) | ref["v"].astype(np.uint32)
+    np.testing.assert_array_equal(_u32(val), want_val)
+    # step 2
+    ph0.sort_pairs(key, val)
+    np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
+    want_sorted_val = (ref["u_sorted"].astype(np.uint32) << 16) | ref["v_sorted"].astype(np.uint32)
+    np.testing.assert_array_equal(_u32(val), want_sorted_val)
+    # step 3
+    a, nd = ph0.dedupe(key)
+    np.testing.assert_array_equal(_u32(a), ref["a"])
+    assert nd == ref["n_distinct"]
+    # steps 4-5
+    bars = ph0.reduce(n, val, a, key)
+    assert_bars_equal(bars.numpy(), ref["bars"])
+    # the whole path in one call
+    whole = ph0.barcodes(pts)
+    assert_bars_equal(whole.numpy(), ref["bars"])
+    assert whole.stats["n_distinct"] == ref["n_distinct"]
+    assert whole.stats["n_bars"] == n - 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 31, 32, 33, 64, 65, 127, 129, 255, 257])
+def test_small_and_ragged_sizes(n):
+    ph0 = _ph0()
+    x = inputs.uniform(n, 3, seed=100 + n)
+    want, inf_v, nd = oracle.barcodes(x)
+    got = ph0.barcodes(_cuda(x))
+    assert_bars_equal(got.numpy(), want)
+    assert inf_v == 0
+
+
+def test_mixture4096_bit_exact():
+    ph0 = _ph0()
+    x = inputs.config_points("mixture4096")
+    want, inf_v, nd = oracle.barcodes(x)
+    got = ph0.barcodes(_cuda(x))
+    assert_bars_equal(got.numpy(), want)
+    assert got.stats["n_distinct"] == nd
+
+
+def test_all_points_equal():
+    ph0 = _ph0()
+    x = np.full((50, 4), 0.25, np.float32)
+    got = ph0.barcodes(_cuda(x)).numpy()
+    assert (got["death_sq"] == 0).all() and (got["a"] == 1).all()
+    assert [(int(b["u"]), int(b["v"])) for b in got] == [(0, j) for j in range(1, 50)]
+
+
+def test_repeat_calls_identical_and_workspace_reuse():
+    ph0 = _ph0()
+    x = inputs.uniform(700, 4, seed=41)
+    ws = ph0.Workspace(700, 4)
+    first = ph0.barcodes(_cuda(x), ws=ws).numpy()
+    y = inputs.uniform(300, 2, seed=42)
+    other = ph0.barcodes(_cuda(y), ws=ws).numpy()
+    again = ph0.barcodes(_cuda(x), ws=ws).numpy()
+    assert_bars_equal(again, first)
+    assert_bars_equal(other, oracle.barcodes(y)[0])
+
+
+def test_nonfinite_input_reported():
+    ph0 = _ph0()
+    from paper_2203_02527_gb300._lib import Ph0Error
+    x = inputs.uniform(40, 3, seed=43)
+    x[7, 1] = np.nan
+    with pytest.raises(Ph0Error) as e:
+        ph0.barcodes(_cuda(x))
+    assert e.value.code == 2
+    x[7, 1] = np.inf
+    with pytest.raises(Ph0Error) as e:
+        ph0.barcodes(_cuda(x))
+    assert e.value.code == 2
+    # the context stays usable
+    y = inputs.uniform(40, 3, seed=44)
+    assert_bars_equal(ph0.barcodes(_cuda(y)).numpy(), oracle.barcodes(y)[0])
+
+
+def test_invalid_arguments():
+    import ctypes
+    from paper_2203_02527_gb300 import _lib
+    lib = _lib.load()
+    assert lib.ph0_workspace_bytes(0, 3) == 0
+    assert lib.ph0_workspace_bytes(65536, 3) == 0
+    assert lib.ph0_workspace_bytes(10, 2000) == 0
+    ws = torch.empty(lib.ph0_workspace_bytes(10, 3), dtype=torch.uint8, device="cuda")
+    pts = torch.zeros((10, 3), device="cuda")
+    bars = torch.empty((9, 40), dtype=torch.uint8, device="cuda")
+    vp = ctypes.c_void_p
+    args = (vp(pts.data_ptr()), 10, 3, 3, vp(bars.data_ptr()), vp(ws.data_ptr()), ws.numel(), None)
+    assert lib.ph0_barcodes(*args) == 0
+    assert lib.ph0_finish(vp(ws.data_ptr()), None, None) == 0
+    assert lib.ph0_barcodes(args[0], 10, 3, 2, *args[4:]) == 1                  # ld < d
+    assert lib.ph0_barcodes(args[0], 0, 3, 3, *args[4:]) == 1                   # n < 1
+    assert lib.ph0_barcodes(args[0], 70000, 3, 3, *args[4:]) == 3               # n too big
+    assert lib.ph0_barcodes(*args[:5], args[5], ws.numel() - 1, None) == 4     # small ws
+    assert lib.ph0_barcodes(*args[:5], vp(ws.data_ptr() + 8), ws.numel(), None) == 1  # misaligned
+
+
+def test_step_oracle_pins_hold_on_gpu_output():
+    # the GPU result satisfies the oracle's independent pins directly
+    ph0 = _ph0()
+    x = inputs.uniform(60, 3, seed=45)
+    got = ph0.barcodes(_cuda(x)).numpy()
+    assert pins.check_bars_structure(60, got, 0) is None
+    assert pins.check_bars_kruskal(x, got) is None
+    assert pins.check_bars_sweep(x[:12], ph0.barcodes(_cuda(x[:12])).numpy()) is None
