@@ -101,9 +101,36 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d);
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                  ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* Device time of each stage of one ph0_barcodes_profiled() call, from CUDA
+ * events recorded on the caller's stream between the stages (milliseconds). */
+typedef struct {
+    float total_ms;          /* first to last event                          */
+    float dist_ms;           /* step 1: distance kernel                       */
+    float sort_ms;           /* step 2: all radix passes                      */
+    float pass_ms[8];        /* step 2: each pass (0 for passes not needed)   */
+    float dedupe_ms;         /* step 3                                        */
+    float reduce_ms;         /* steps 4-5: pivot claiming                     */
+    float emit_ms;           /* ordering of the pivot columns and bar output  */
+} ph0_profile;
+
+/* ph0_barcodes() with a CUDA event between stages; waits for the stream and
+ * fills `prof` (tracing aid: same kernels, same results). */
+int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                          ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
+                          ph0_profile *prof);
+
 /* Waits for `stream`, then returns the device status of the last call made
  * with `ws` and, when stats != NULL, its counters. */
 int ph0_finish(const void *ws, void *stream, ph0_stats *stats);
+
+/* Tracing aid: copies to `out` (host, max_windows x 12 uint64) the per-window
+ * records of the last reduction run on `ws` for a cloud of (n, d):
+ * {first position, window size, candidates, grid-wide rounds, shared-memory
+ *  rounds, pivots so far, then globaltimer stamps (ns): begin, filtered,
+ *  grid rounds done, shared-memory rounds done, end}.  Unused records are 0.
+ * Waits for `stream`. */
+int ph0_trace_windows(const void *ws, int64_t n, int32_t d, void *stream, uint64_t *out,
+                      int32_t max_windows);
 
 /* ---- step entry points (each one step of the path, for testing and reuse) ---- */
 

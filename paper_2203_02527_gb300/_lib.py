@@ -48,6 +48,19 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("total_ms", ctypes.c_float), ("dist_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
+        ("pass_ms", ctypes.c_float * 8), ("dedupe_ms", ctypes.c_float),
+        ("reduce_ms", ctypes.c_float), ("emit_ms", ctypes.c_float),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pass_ms"}
+        d["pass_ms"] = list(self.pass_ms)
+        return d
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -60,6 +73,9 @@ SIGNATURES = {
     "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
     "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
+    "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
+                                             ctypes.POINTER(Profile)]),
+    "ph0_trace_windows": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32]),
     "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_sort": (ctypes.c_int, [_VP, _VP, _I64, _VP, _SZ, _VP]),
     "ph0_dedupe": (ctypes.c_int, [_VP, _I64, _VP, _VP, _SZ, _VP]),

@@ -27,12 +27,18 @@
 //               endpoints; equal roots -> zero column.  Otherwise it claims
 //               both root slots with an atomic minimum of its position
 //               (priority to the lower filtration position).  A column that
-//               holds both slots is the first remaining column touching
-//               either component, so in the left-to-right order nothing
-//               before it changes them: it is nonzero, its pivot is the larger
-//               root, and it links that root under the smaller one.  Columns
-//               that lost a slot to a lower position retry in the next round.
-//               Each round the lowest remaining column wins, so rounds end.
+//               holds the slot of the larger root H is the first remaining
+//               column touching H's component, so in the left-to-right order
+//               nothing before it changes that component, whose minimum is H;
+//               and every link made so far on the path from its other endpoint
+//               to that endpoint's (smaller) root comes from an earlier column
+//               (each link is made by the first remaining column touching the
+//               linked component).  So the column is nonzero with pivot H; it
+//               links H under the smaller root, which keeps every root the
+//               minimum of its component.  Other columns retry next round.
+//               Each round the lowest remaining column holds its larger root,
+//               so the rounds end.  Once at most kTailCap columns are left, one
+//               CTA finishes the window's rounds in shared memory.
 //   flatten     every vertex's root is updated.
 // Early exit: once n-1 pivots exist every later column is zero (the graph is
 // connected); the window loop stops.
@@ -51,6 +57,7 @@ constexpr uint32_t kDead = 0xffffffffu;
 __global__ void k_reduce_init(ReduceArgs A) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = tid; i < int64_t(kTraceWindows) * kTraceWords; i += stride) A.trace[i] = 0;
     for (int64_t v = tid; v < A.n; v += stride) {
         A.comp[v] = uint32_t(v);
         A.parent[v] = uint32_t(v);
@@ -123,6 +130,144 @@ __device__ __forceinline__ void warp_append(bool take, uint32_t p, uint32_t *lis
     if (take) list[base + __popc(mask & ((1u << lane) - 1u))] = p;
 }
 
+
+__device__ __forceinline__ void record_pivot(const ReduceArgs &A, Header *h, uint32_t target,
+                                             uint32_t p, uint32_t low) {
+    const uint32_t j = atomicAdd(&h->npiv, 1u);
+    if (j < target) {
+        A.kill_key[j] = p;
+        A.kill_val[j] = low;
+    } else {
+        set_status(h, PH0_EINTERNAL);
+    }
+}
+
+__device__ __forceinline__ uint16_t local_find(uint16_t *par, uint16_t x) {
+    for (;;) {
+        const uint16_t p = par[x];
+        if (p == x) return x;
+        const uint16_t g = par[p];
+        par[x] = g;  // path halving (benign race: only moves toward the root)
+        x = g;
+    }
+}
+
+// The candidate rounds of one window, run by a single CTA (all threads) in
+// shared memory once at most kTailCap candidates are left.  Same rules as the
+// grid rounds; the current roots of the candidates' endpoints get local ids
+// (the snapshot array is reused as the global->local map), so every find,
+// claim and link is a shared-memory access and rounds are separated by
+// __syncthreads instead of grid barriers.  Returns the number of rounds.
+__device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *val,
+                                const uint32_t *list, uint32_t ncur, uint16_t *s_comp,
+                                unsigned char *s_tail, uint32_t target) {
+    constexpr int C = kTailCap;
+    uint32_t *s_p = reinterpret_cast<uint32_t *>(s_tail);        // [C] position
+    uint32_t *s_lres = s_p + C;                                   // [2C] claim per local root
+    uint16_t *s_lu = reinterpret_cast<uint16_t *>(s_lres + 2 * C);  // [C] local root, u side
+    uint16_t *s_lv = s_lu + C;                                    // [C] local root, v side
+    uint16_t *s_ra = s_lv + C;                                    // [C] this round's roots
+    uint16_t *s_rb = s_ra + C;
+    uint16_t *s_lpar = s_rb + C;                                  // [2C] local parent
+    uint16_t *s_gid = s_lpar + 2 * C;                             // [2C] global id
+    uint8_t *s_act = reinterpret_cast<uint8_t *>(s_gid + 2 * C);  // [C] still active
+    __shared__ uint32_t s_nroots, s_left;
+    const int tid = threadIdx.x;
+    const int T = blockDim.x;
+    if (tid == 0) {
+        s_nroots = 0;
+        s_left = 0;
+    }
+    // global roots and window-start roots of every endpoint
+    for (uint32_t i = tid; i < ncur; i += T) {
+        const uint32_t p = __ldcg(list + i);
+        const uint32_t vv = val[p];
+        const uint32_t u = vv >> 16, v = vv & 0xffffu;
+        s_p[i] = p;
+        s_ra[i] = uint16_t(find_root(A.parent, __ldcg(A.comp + u)));
+        s_rb[i] = uint16_t(find_root(A.parent, __ldcg(A.comp + v)));
+        s_act[i] = 1;
+    }
+    __syncthreads();
+    // local ids: s_comp becomes the map global root -> local id
+    for (uint32_t i = tid; i < ncur; i += T) {
+        s_comp[s_ra[i]] = 0xffffu;
+        s_comp[s_rb[i]] = 0xffffu;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < ncur; i += T) {
+        for (int side = 0; side < 2; ++side) {
+            const uint16_t g = side ? s_rb[i] : s_ra[i];
+            if (atomicCAS(reinterpret_cast<unsigned short *>(s_comp + g), (unsigned short)0xffffu,
+                          (unsigned short)0xfffeu) == 0xffffu) {
+                const uint32_t id = atomicAdd(&s_nroots, 1u);
+                s_gid[id] = g;
+                s_lpar[id] = uint16_t(id);
+                s_lres[id] = 0xffffffffu;
+                s_comp[g] = uint16_t(id);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < ncur; i += T) {
+        s_lu[i] = s_comp[s_ra[i]];
+        s_lv[i] = s_comp[s_rb[i]];
+    }
+    __syncthreads();
+    uint32_t rounds = 0;
+    for (;;) {
+        ++rounds;
+        for (uint32_t i = tid; i < ncur; i += T) {
+            if (!s_act[i]) continue;
+            const uint16_t a = local_find(s_lpar, s_lu[i]), b = local_find(s_lpar, s_lv[i]);
+            if (a == b) {
+                s_act[i] = 0;
+                continue;
+            }
+            s_ra[i] = a;
+            s_rb[i] = b;
+            atomicMin(s_lres + a, s_p[i]);
+            atomicMin(s_lres + b, s_p[i]);
+        }
+        __syncthreads();
+        uint32_t left = 0;
+        for (uint32_t i = tid; i < ncur; i += T) {
+            if (!s_act[i]) continue;
+            const uint16_t a = s_ra[i], b = s_rb[i];
+            const uint32_t p = s_p[i];
+            const bool a_lo = s_gid[a] < s_gid[b];
+            const uint16_t lo = a_lo ? a : b, hi = a_lo ? b : a;
+            if (s_lres[hi] == p) {
+                s_lpar[hi] = lo;
+                s_act[i] = 0;
+                record_pivot(A, h, target, p, s_gid[hi]);
+            } else {
+                ++left;
+            }
+        }
+        if (left) atomicAdd(&s_left, left);
+        __syncthreads();
+        for (uint32_t r = tid; r < s_nroots; r += T) s_lres[r] = 0xffffffffu;
+        const uint32_t remaining = s_left;
+        __syncthreads();
+        if (tid == 0) s_left = 0;
+        if (remaining == 0) break;
+        __syncthreads();
+    }
+    // write the links back to the global root table
+    __syncthreads();
+    for (uint32_t r = tid; r < s_nroots; r += T)
+        if (s_lpar[r] != r) A.parent[s_gid[r]] = s_gid[s_lpar[r]];
+    __syncthreads();
+    return rounds;
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     extern __shared__ uint16_t s_comp[];  // [n] root snapshot of the window
     __shared__ uint32_t s_hkey[kHashSize], s_hval[kHashSize];
@@ -141,7 +286,8 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     const uint32_t target = uint32_t(n - 1);
 
     int64_t pos0 = 0, W = A.w0;
-    uint32_t round = 0;
+    uint32_t round = 0;       // grid rounds: identical in every CTA (claim tags)
+    int64_t tail_total = 0;   // shared-memory rounds (CTA 0)
     int windows = 0;
     int64_t candidates = 0;
     for (;;) {
@@ -149,6 +295,15 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         if (pos0 >= m || npiv >= target) break;
         const int64_t wend = (m - pos0 < W) ? m : pos0 + W;
         ++windows;
+        const bool tr = blockIdx.x == 0 && tid == 0 && windows <= kTraceWindows;
+        uint64_t *rec = A.trace + size_t(windows - 1) * kTraceWords;
+        const uint32_t round_before = round;
+        const int64_t tail_before = tail_total;
+        if (tr) {
+            rec[0] = pos0;
+            rec[1] = W;
+            rec[6] = gtimer();
+        }
 
         // ---------------- F: filter the window against the snapshot -------
         for (int64_t v = tid; v < n; v += kReduceThreads) s_comp[v] = uint16_t(__ldcg(A.comp + v));
@@ -202,14 +357,18 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         uint32_t ncur = __ldcg(&h->nlist[0]);
         const uint32_t nwin = ncur;
         candidates += nwin;
-        while (ncur > 0) {
+        if (tr) {
+            rec[2] = nwin;
+            rec[7] = gtimer();
+        }
+        while (ncur > uint32_t(kTailCap)) {
             ++round;
             const unsigned long long tag = (unsigned long long)(0xffffffffu - round) << 32;
             const uint32_t *list = cur ? A.cand1 : A.cand0;
             uint32_t *next = cur ? A.cand0 : A.cand1;
             uint32_t *next_count = &h->nlist[cur ^ 1];
             if (blockIdx.x == 0 && tid == 0) *next_count = 0;
-            // reserve both roots
+            // claim both current roots
             for (int64_t i = gtid; i < ncur; i += gstride) {
                 const uint32_t p = __ldcg(list + i);
                 const uint32_t vv = val[p];
@@ -224,7 +383,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 }
             }
             if (!grid_barrier(h, &s_ok)) return;
-            // commit the columns that hold both roots
+            // commit the columns that hold their larger root H: pivot H
             for (int64_t b = int64_t(blockIdx.x) * kReduceThreads; b < ncur; b += gstride) {
                 const int64_t i = b + tid;
                 bool keep = false;
@@ -234,17 +393,10 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                     if (r != kDead) {
                         p = __ldcg(list + i);
                         const uint32_t ru = r >> 16, rv = r & 0xffffu;
-                        const unsigned long long mine = tag | p;
-                        if (__ldcg(A.res + ru) == mine && __ldcg(A.res + rv) == mine) {
-                            const uint32_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
+                        const uint32_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
+                        if (__ldcg(A.res + hi) == (tag | p)) {
                             A.parent[hi] = lo;
-                            const uint32_t j = atomicAdd(&h->npiv, 1u);
-                            if (j < target) {
-                                A.kill_key[j] = p;
-                                A.kill_val[j] = hi;
-                            } else {
-                                set_status(h, PH0_EINTERNAL);
-                            }
+                            record_pivot(A, h, target, p, hi);
                         } else {
                             keep = true;
                         }
@@ -256,13 +408,29 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             cur ^= 1;
             ncur = __ldcg(&h->nlist[cur]);
         }
+        if (tr) rec[8] = gtimer();
+        if (ncur > 0) {
+            // few candidates left: one CTA finishes the window in shared memory
+            if (blockIdx.x == 0)
+                tail_total += tail_rounds(A, h, val, cur ? A.cand1 : A.cand0, ncur, s_comp,
+                                          reinterpret_cast<unsigned char *>(s_comp + ((n + 7) & ~int64_t(7))),
+                                          target);
+            if (!grid_barrier(h, &s_ok)) return;
+        }
 
+        if (tr) rec[9] = gtimer();
         // ---------------- flatten the roots -----------------------------------
         for (int64_t v = gtid; v < n; v += gstride)
             A.comp[v] = find_root(A.parent, __ldcg(A.comp + v));
         if (blockIdx.x == 0 && tid == 0) h->nlist[0] = 0;
         if (!grid_barrier(h, &s_ok)) return;
 
+        if (tr) {
+            rec[3] = round - round_before;
+            rec[4] = uint64_t(tail_total - tail_before);
+            rec[5] = __ldcg(&h->npiv);
+            rec[10] = gtimer();
+        }
         pos0 = wend;
         if (nwin * 64 < W) W *= 8;
         else if (nwin * 8 < W) W *= 4;
@@ -273,7 +441,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         h->windows = windows;
         h->edges_scanned = pos0;
         h->candidates = candidates;
-        h->rounds = round;
+        h->rounds = int64_t(round) + tail_total;
         h->n_bars = __ldcg(&h->npiv);
     }
 }
@@ -311,6 +479,13 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
 // ------------------------------------------------------------------ host ---
 int sm_count();
 
+// Snapshot labels (2 B per vertex, rounded up to 16 B) plus the tail arrays.
+size_t reduce_dyn_smem(int64_t n) {
+    const size_t snap = sizeof(uint16_t) * size_t((n + 7) & ~int64_t(7));
+    const size_t tail = size_t(kTailCap) * (4 + 4 * 2 + 2 * 4 + 2 * 2 * 2 + 1);
+    return snap + tail;
+}
+
 cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     int blocks = int((A.n + 255) / 256);
     if (blocks < 1) blocks = 1;
@@ -319,7 +494,7 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || A.m <= 0) return e;
 
-    const size_t smem = sizeof(uint16_t) * size_t(A.n);
+    const size_t smem = reduce_dyn_smem(A.n);
     e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;

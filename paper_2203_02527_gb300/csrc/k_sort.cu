@@ -302,6 +302,19 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
     return cudaSuccess;
 }
 
+const void *k_onesweep_symbol() { return (const void *)k_onesweep; }
+size_t sort_dyn_smem() { return kSortDynSmem; }
+
+// One pass (the attribute for the dynamic shared memory must be set).
+cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                             int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
+                             cudaStream_t s) {
+    const int64_t tiles = (m + kSortTile - 1) / kSortTile;
+    k_onesweep<<<unsigned(tiles), kSortThreads, kSortDynSmem, s>>>(keys0, keys1, vals0, vals1, m, pass,
+                                                                    look0, look1, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;

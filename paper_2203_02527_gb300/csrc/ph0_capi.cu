@@ -16,6 +16,11 @@ cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStre
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
                                cudaStream_t s);
+cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                             int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
+                             cudaStream_t s);
+const void *k_onesweep_symbol();
+size_t sort_dyn_smem();
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
@@ -62,7 +67,8 @@ cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s) {
 // (sort_h != null selects the one holding the sorted data) or the caller's.
 cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
                             const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
-                            const Header *sort_h, const uint32_t *a, ph0_bar *bars, cudaStream_t s) {
+                            const Header *sort_h, const uint32_t *a, ph0_bar *bars, cudaStream_t s,
+                            cudaEvent_t after_reduce = nullptr) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t m = n_edges(n);
     ReduceArgs A;
@@ -80,10 +86,15 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
     A.kill_key = at<unsigned long long>(ws, L.kill_key[0]);
     A.kill_val = at<uint32_t>(ws, L.kill_val[0]);
     A.h = h;
+    A.trace = at<uint64_t>(ws, L.trace);
     int64_t w0 = 2 * n > 4096 ? 2 * n : 4096;
     A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
     cudaError_t e = launch_reduce(A, s);
     if (e != cudaSuccess) return e;
+    if (after_reduce) {
+        e = cudaEventRecord(after_reduce, s);
+        if (e != cudaSuccess) return e;
+    }
     const int64_t nb = n - 1;
     if (nb <= 0) return cudaSuccess;
     // order the n-1 pivot columns by sorted position (their discovery order
@@ -158,6 +169,67 @@ int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar
     return cuda_status(e);
 }
 
+int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                          ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
+                          ph0_profile *prof) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (!pts_dev || !ws || !prof || (n > 1 && !bars_dev)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint32_t *a = at<uint32_t>(ws, L.a);
+    uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
+    constexpr int kEv = 6 + kMaxPasses;
+    cudaEvent_t ev[kEv];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < kEv && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < made - 1; ++i) cudaEventDestroy(ev[i]);
+        return PH0_ECUDA;
+    }
+    // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | dedupe | ev[2+P] | reduce | ev[3+P] |
+    // order pivots, emit | ev[4+P]   (P = kMaxPasses launches; unneeded passes return at once)
+    e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = begin_call(ws, L, s);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess && L.m > 0)
+        e = cudaFuncSetAttribute(k_onesweep_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sort_dyn_smem()));
+    for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
+        if (L.m > 0) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
+    }
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s, ev[3 + kMaxPasses]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 + kMaxPasses], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4 + kMaxPasses]);
+    if (e == cudaSuccess) {
+        auto span = [&](int i, int j) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[j]);
+            return ms;
+        };
+        std::memset(prof, 0, sizeof(*prof));
+        prof->total_ms = span(0, 4 + kMaxPasses);
+        prof->dist_ms = span(0, 1);
+        for (int p = 0; p < kMaxPasses; ++p) prof->pass_ms[p] = span(1 + p, 2 + p);
+        prof->sort_ms = span(1, 1 + kMaxPasses);
+        prof->dedupe_ms = span(1 + kMaxPasses, 2 + kMaxPasses);
+        prof->reduce_ms = span(2 + kMaxPasses, 3 + kMaxPasses);
+        prof->emit_ms = span(3 + kMaxPasses, 4 + kMaxPasses);
+    }
+    for (int i = 0; i < kEv; ++i) cudaEventDestroy(ev[i]);
+    return cuda_status(e);
+}
+
 int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
     if (!ws) return PH0_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -178,6 +250,20 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
         stats->n_bars = hh.n_bars;
     }
     return hh.status;
+}
+
+int ph0_trace_windows(const void *ws, int64_t n, int32_t d, void *stream, uint64_t *out,
+                      int32_t max_windows) {
+    int rc = check_sizes(n, d, d);
+    if (rc != PH0_OK) return rc;
+    if (!ws || !out || max_windows < 0) return PH0_EINVAL;
+    const Layout L(n, d);
+    const int w = max_windows < kTraceWindows ? max_windows : kTraceWindows;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, static_cast<const char *>(ws) + L.trace,
+                       sizeof(uint64_t) * kTraceWords * size_t(w), cudaMemcpyDeviceToHost);
+    return cuda_status(e);
 }
 
 int ph0_distances(const float *pts_dev, int64_t n, int32_t d, int64_t ld, uint64_t *key_dev,

@@ -69,7 +69,14 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) {
 __host__ __device__ inline int64_t n_edges(int64_t n) { return n * (n - 1) / 2; }
 
 // Candidate list capacity of one reduction window (edges per window).
-constexpr int64_t kMaxWindow = int64_t(1) << 22;
+constexpr int64_t kMaxWindow = int64_t(1) << 26;
+// Trace of the reduction: kTraceWindows records of kTraceWords words:
+// {pos0, window size, candidates, grid rounds, tail rounds, pivots after,
+//  t_begin, t_filtered, t_grid_done, t_tail_done, t_end} (globaltimer, ns).
+constexpr int kTraceWindows = 256;
+constexpr int kTraceWords = 12;
+// Candidate count at or below which one CTA finishes a window in shared memory.
+constexpr int kTailCap = 2048;
 
 // Byte offsets of every region of the workspace for a cloud of n points in
 // dimension d.  Everything is caller-owned device memory; nothing is
@@ -82,6 +89,7 @@ struct Layout {
     size_t comp, parent, res, cand[2], candr;
     size_t kill_key[2], kill_val[2], kill_look[2];
     size_t grad;                         // binary64 gradient accumulator [n, d]
+    size_t trace;                        // per-window trace records of the reduction
     size_t total;
 
     __host__ __device__ Layout(int64_t n_, int32_t d_) : n(n_) {
@@ -118,6 +126,7 @@ struct Layout {
         kill_look[0] = take(8 * size_t(ktiles) * kRadix);
         kill_look[1] = take(8 * size_t(ktiles) * kRadix);
         grad = take(8 * size_t(n) * size_t(d_ > 0 ? d_ : 1));
+        trace = take(sizeof(uint64_t) * kTraceWords * kTraceWindows);
         total = off;
     }
 };
@@ -136,6 +145,7 @@ struct ReduceArgs {
     uint32_t *kill_val;            // [n] its pivot row
     Header *h;
     int64_t w0;                    // first window size
+    uint64_t *trace;               // [kTraceWindows][kTraceWords]
 };
 
 template <typename T>

@@ -108,6 +108,36 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     return Bars(bars, n, st)
 
 
+def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None):
+    """ph0_barcodes with CUDA events between the stages (waits for the stream).
+    Returns (Bars, per-stage milliseconds)."""
+    pts, n, d, ld = _points(pts)
+    ws = ws or _workspace(n, d, pts.device)
+    if bars is None:
+        bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
+    prof = _lib.Profile()
+    check(_lib.load().ph0_barcodes_profiled(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes,
+                                            _stream(), ctypes.byref(prof)), "ph0_barcodes_profiled")
+    return Bars(bars, n, None), prof.as_dict()
+
+
+def trace_windows(ws: Workspace, n: int, d: int, max_windows: int = 256):
+    """Per-window records of the last reduction on `ws` (tracing aid)."""
+    out = np.zeros((max_windows, 12), np.uint64)
+    check(_lib.load().ph0_trace_windows(ws.ptr, n, d, _stream(), out.ctypes.data_as(ctypes.c_void_p),
+                                        max_windows), "ph0_trace_windows")
+    rows = []
+    for r in out:
+        if r[1] == 0:
+            break
+        t0 = int(r[6])
+        rows.append({"pos0": int(r[0]), "window": int(r[1]), "candidates": int(r[2]),
+                     "grid_rounds": int(r[3]), "tail_rounds": int(r[4]), "pivots": int(r[5]),
+                     "filter_us": (int(r[7]) - t0) / 1e3, "grid_us": (int(r[8]) - int(r[7])) / 1e3,
+                     "tail_us": (int(r[9]) - int(r[8])) / 1e3, "flatten_us": (int(r[10]) - int(r[9])) / 1e3})
+    return rows
+
+
 def finish(ws: Workspace) -> dict:
     st = Stats()
     rc = _lib.load().ph0_finish(ws.ptr, _stream(), ctypes.byref(st))
