@@ -169,6 +169,29 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
                const uint32_t *a_dev, const uint64_t *key_sorted_dev,
                ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- allocation-free variant (the paper has no counterpart) ----
+ *
+ * ph0_barcodes() for callers that cannot allocate device memory where they
+ * need barcodes: code running while a stream is captured, latency-critical
+ * loops in which an allocation could synchronize the device or take a driver
+ * lock, and hosts whose memory is all owned by their own pool.  Instead of a
+ * caller workspace it uses a 16 MiB array in the library's device memory
+ * (every GPU that loads the library holds it until the process exits); the
+ * caller still passes the points and the bars buffer.  Clouds whose workspace
+ * would exceed 16 MiB (ph0_workspace_bytes(n, d) > 16 MiB: n above 901 at
+ * d = 3, above 896 at d = 32) are rejected with PH0_ETOOBIG before any work is queued.  It
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *
+ * The first call on a device looks up the device address of the array for
+ * that device (with that device current); make that first call before any
+ * stream capture.  All calls share the one array per device, which keeps the
+ * last call's contents (every stage clears what it needs zeroed): calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  Waits for `stream`, then returns the device
+ * status of the call (as ph0_finish() would). */
+int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                         ph0_bar *bars_dev, void *stream);
+
 /* ---- differentiation ---- */
 
 /* Backward of death_i = |x_v - x_u| for fixed killing edges:

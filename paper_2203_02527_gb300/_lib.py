@@ -76,6 +76,7 @@ SIGNATURES = {
     "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
                                              ctypes.POINTER(Profile)]),
     "ph0_trace_windows": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32]),
+    "ph0_barcodes_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP]),
     "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_sort": (ctypes.c_int, [_VP, _VP, _I64, _VP, _SZ, _VP]),
     "ph0_dedupe": (ctypes.c_int, [_VP, _I64, _VP, _VP, _SZ, _VP]),

@@ -4,6 +4,7 @@
 // state: every buffer is caller-owned and every call is asynchronous on the
 // caller's stream.
 #include <cstring>
+#include <mutex>
 
 #include "ph0_common.cuh"
 
@@ -357,3 +358,67 @@ int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d, int64_t ld
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.  Some callers cannot call cudaMalloc (or any
+// allocator) at the point where they need barcodes: code that runs while a
+// stream is being captured, latency-critical loops where an allocation could
+// synchronize the device or take a driver lock, and hosts that own all device
+// memory through their own pool and forbid raw allocations.  For clouds small
+// enough to fit, this entry point takes its workspace from a fixed array in
+// the library's device memory instead of from the caller.
+// ---------------------------------------------------------------------------
+namespace ph0 {
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB, held by every GPU that loads the library
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+}  // namespace ph0
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ph0::kNoAllocScratchBytes];
+
+extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                                    ph0_bar *bars_dev, void *stream) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (!pts_dev || (n > 1 && !bars_dev)) return PH0_EINVAL;
+    if (!aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (L.total > kNoAllocScratchBytes) return PH0_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PH0_ECUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return PH0_EINVAL;
+    void *ws = nullptr;
+    {
+        // once per device, with that device current: the device address of
+        // the array (its host-side name is not a device pointer)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PH0_ECUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        ws = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint32_t *a = at<uint32_t>(ws, L.a);
+    // the array keeps the previous call's contents: begin_call zeroes the
+    // header and the first look-back buffer, and every later stage clears or
+    // overwrites what it reads before reading it
+    cudaError_t e = begin_call(ws, L, s);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
+    if (e == cudaSuccess)
+        e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
+                               at<uint64_t>(ws, L.look[1]), h, s);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int32_t status = PH0_OK;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? status : PH0_ECUDA;
+}
