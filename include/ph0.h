@@ -81,6 +81,8 @@ typedef struct {
     int64_t candidates;      /* edges that reached the pivot-claiming rounds  */
     int64_t rounds;          /* pivot-claiming rounds over all windows        */
     int64_t n_bars;          /* finite bars written                           */
+    int64_t dist_tiles;      /* distance tiles                                */
+    int64_t dist_tiles_int;  /* ... of which computed on the integer path     */
 } ph0_stats;
 
 /* Human-readable name of a status code (static storage). */

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
         ("key_bits", ctypes.c_int32), ("windows", ctypes.c_int32),
         ("n_distinct", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
         ("candidates", ctypes.c_int64), ("rounds", ctypes.c_int64),
-        ("n_bars", ctypes.c_int64),
+        ("n_bars", ctypes.c_int64), ("dist_tiles", ctypes.c_int64),
+        ("dist_tiles_int", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -9,13 +9,27 @@
 // and the u coordinate is a broadcast.  A warp writes 32 consecutive edges of
 // one row u, so the key (8 B) and val (4 B) stores are coalesced.
 //
+// The arithmetic: when, in every dimension, the tile's coordinates are exact
+// integers times a common power of two with magnitudes below 2^52 (checked
+// per tile), the rounded binary64 sequence is computed bit-identically with
+// integer arithmetic (emu64.cuh) for half of the tile's rows and with the
+// binary64 units for the other half, because the binary64 units of this GPU
+// run at 1/64 of the integer rate and the two pipes overlap; otherwise the
+// whole tile uses the binary64 units.
+//
 // Fused: the histogram of the low 8 key bits (radix pass 0), the min and max
 // key (the sort's bit range), and the finiteness check of the input.
+#include "emu64.cuh"
 #include "ph0_common.cuh"
 
 namespace ph0 {
 
 constexpr int kDistThreads = 256;
+// On integer-path tiles, rows i with (i % 16) < kDistHwRows16 still use the
+// binary64 units: the two pipes run concurrently, and an even split measured
+// fastest on GB300 (30 ms vs 46 ms integer-only and 50 ms binary64-only for
+// 537M edges at d = 16).  Both paths give identical bits.
+constexpr int kDistHwRows16 = 8;
 
 // Squared distance of one edge: s = 0; t = x_v - x_u; s = s + t*t per
 // dimension, each operation rounded to nearest (no contraction).
@@ -45,11 +59,14 @@ __device__ __forceinline__ void tile_coords(int64_t lin, int64_t T, int64_t &bi,
 }
 
 __global__ void __launch_bounds__(kDistThreads)
-k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt,
+k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16,
        uint64_t *__restrict__ key, uint32_t *__restrict__ val, Header *__restrict__ h) {
-    extern __shared__ double s_coord[];  // [d][bt] for u block, then [d][bt] for v block
+    // [d][bt] u block, then [d][bt] v block: binary64 values, or int64 fixed
+    // point in units of 2^g[k] on the integer path; then g[d], lo[d], hi[d]
+    extern __shared__ double s_coord[];
     __shared__ uint32_t s_hist[kRadix];
     __shared__ uint64_t s_min[kDistThreads / 32], s_max[kDistThreads / 32];
+    __shared__ int s_fixed;
 
     const int64_t T = (n + bt - 1) / bt;
     int64_t bi, bj;
@@ -57,18 +74,67 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt,
     const int u0 = int(bi) * bt, v0 = int(bj) * bt;
     double *su = s_coord;
     double *sv = s_coord + size_t(d) * bt;
+    int64_t *xu = reinterpret_cast<int64_t *>(su);
+    int64_t *xv = reinterpret_cast<int64_t *>(sv);
+    double *fu = s_coord + size_t(2) * d * bt;      // binary64 copies for the split rows
+    double *fv = fu + size_t(d) * bt;
+    int32_t *s_g = reinterpret_cast<int32_t *>(s_coord + size_t(4) * d * bt);
+    int32_t *s_lo = s_g + d;
+    int32_t *s_hi = s_lo + d;
 
     for (int b = threadIdx.x; b < kRadix; b += blockDim.x) s_hist[b] = 0;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        s_lo[k] = 1 << 30;
+        s_hi[k] = -(1 << 30);
+    }
+    __syncthreads();
+    // pass 1: finiteness and, per dimension, the span of set bits
     bool bad = false;
-    for (int idx = threadIdx.x; idx < bt * d; idx += blockDim.x) {
-        int p = idx / d, k = idx % d;
-        float xu = (u0 + p < n) ? pts[int64_t(u0 + p) * ld + k] : 0.0f;
-        float xv = (v0 + p < n) ? pts[int64_t(v0 + p) * ld + k] : 0.0f;
-        bad |= !isfinite(xu) || !isfinite(xv);
-        su[k * bt + p] = double(xu);
-        sv[k * bt + p] = double(xv);
+    for (int idx = threadIdx.x; idx < 2 * bt * d; idx += blockDim.x) {
+        const int side = idx / (bt * d), r = idx % (bt * d);
+        const int p = r / d, k = r % d;
+        const int row = (side ? v0 : u0) + p;
+        const float x = row < n ? pts[int64_t(row) * ld + k] : 0.0f;
+        const uint32_t b = __float_as_uint(x);
+        if ((b & 0x7f800000u) == 0x7f800000u) {
+            bad = true;
+        } else if (b & 0x7fffffffu) {
+            int32_t lo, hi;
+            emu::bit_range_f32(b, lo, hi);
+            atomicMin(s_lo + k, lo);
+            atomicMax(s_hi + k, hi);
+        }
     }
     if (bad) set_status(h, PH0_ENONFINITE);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fixed = 1;
+        for (int k = 0; k < d; ++k) {
+            const bool zero = s_lo[k] == (1 << 30);
+            s_g[k] = zero ? 0 : s_lo[k];
+            if (!zero && s_hi[k] + 1 - s_lo[k] > 52) fixed = 0;
+        }
+        s_fixed = fixed;
+        atomicAdd(&h->dist_tiles, 1ull);
+        if (fixed) atomicAdd(&h->dist_tiles_exact_int, 1ull);
+    }
+    __syncthreads();
+    const bool fixed = s_fixed != 0;
+    // pass 2: stage the coordinates, dimension-major
+    for (int idx = threadIdx.x; idx < bt * d; idx += blockDim.x) {
+        const int p = idx / d, k = idx % d;
+        const float a = (u0 + p < n) ? pts[int64_t(u0 + p) * ld + k] : 0.0f;
+        const float b = (v0 + p < n) ? pts[int64_t(v0 + p) * ld + k] : 0.0f;
+        if (fixed) {
+            xu[k * bt + p] = emu::to_fixed(__float_as_uint(a), s_g[k]);
+            xv[k * bt + p] = emu::to_fixed(__float_as_uint(b), s_g[k]);
+            fu[k * bt + p] = double(a);
+            fv[k * bt + p] = double(b);
+        } else {
+            su[k * bt + p] = double(a);
+            sv[k * bt + p] = double(b);
+        }
+    }
     __syncthreads();
 
     uint64_t kmin = ~0ull, kmax = 0;
@@ -78,8 +144,10 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt,
     for (int i = threadIdx.x / bt; i < bt; i += rows_per_pass) {
         const int u = u0 + i;
         if (u < v && v < n) {
-            double s = sq_dist_f64(su, sv, d, bt, i, j);
-            uint64_t kb = uint64_t(__double_as_longlong(s));
+            uint64_t kb;
+            if (!fixed) kb = uint64_t(__double_as_longlong(sq_dist_f64(su, sv, d, bt, i, j)));
+            else if ((i & 15) < hw16) kb = uint64_t(__double_as_longlong(sq_dist_f64(fu, fv, d, bt, i, j)));
+            else kb = emu::sq_dist_fixed(xu + i, xv + j, s_g, d, bt, bt);
             int64_t e = edge_index(n, u, v);
             key[e] = kb;
             val[e] = (uint32_t(u) << 16) | uint32_t(v);
@@ -114,10 +182,15 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt,
         if (s_hist[b]) atomicAdd(&h->hist[0][b], s_hist[b]);
 }
 
-// Tile edge for dimension d: the two staged blocks must fit in shared memory.
+// Shared memory of a tile: two staged blocks plus g, lo, hi per dimension.
+size_t dist_smem(int bt, int d) {
+    return size_t(4) * bt * d * sizeof(double) + size_t(3) * d * sizeof(int32_t);
+}
+
+// Tile edge for dimension d: the staged blocks must fit in shared memory.
 int dist_tile(int d) {
     int bt = 128;
-    while (bt > 8 && size_t(2) * bt * d * sizeof(double) > 160 * 1024) bt /= 2;
+    while (bt > 8 && dist_smem(bt, d) > 160 * 1024) bt /= 2;
     return bt;
 }
 
@@ -125,14 +198,15 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
                         uint32_t *val, Header *h, cudaStream_t s) {
     if (n < 2) return cudaSuccess;
     const int bt = dist_tile(d);
-    const size_t smem = size_t(2) * bt * d * sizeof(double);
+    const size_t smem = dist_smem(bt, d);
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_dist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          160 * 1024);
     if (e != cudaSuccess) return e;
     const int64_t T = (n + bt - 1) / bt;
     const int64_t tiles = T * (T + 1) / 2;
-    k_dist<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, key, val, h);
+    k_dist<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, kDistHwRows16, key,
+                                                       val, h);
     return cudaGetLastError();
 }
 

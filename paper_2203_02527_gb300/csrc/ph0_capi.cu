@@ -249,6 +249,8 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
         stats->candidates = hh.candidates;
         stats->rounds = hh.rounds;
         stats->n_bars = hh.n_bars;
+        stats->dist_tiles = int64_t(hh.dist_tiles);
+        stats->dist_tiles_int = int64_t(hh.dist_tiles_exact_int);
     }
     return hh.status;
 }

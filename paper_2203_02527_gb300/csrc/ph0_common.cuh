@@ -48,6 +48,8 @@ struct Header {
     int64_t candidates;
     int64_t rounds;
     int64_t n_bars;
+    unsigned long long dist_tiles;        // distance tiles, and those on the integer path
+    unsigned long long dist_tiles_exact_int;
     uint32_t tile_counter[kMaxPasses + 4];
     // grid barrier of the persistent reduction kernel
     uint32_t bar_count;
