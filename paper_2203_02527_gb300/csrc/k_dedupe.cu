@@ -6,8 +6,9 @@
 // equality of the binary64 bit patterns), and a[p] = flag[0] + ... + flag[p]
 // is an inclusive prefix sum, computed in one pass: each CTA scans a tile in
 // shared memory and obtains the count of all earlier tiles by decoupled
-// look-back (bounded waits).  Loads and stores are staged through shared
-// memory so that global accesses are coalesced.
+// look-back (bounded waits).  Items are striped over the threads (warp
+// ballots count the new values), so every global and shared access is
+// coalesced and free of bank conflicts.
 #include "ph0_common.cuh"
 
 namespace ph0 {
@@ -21,9 +22,8 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
          uint32_t *__restrict__ a, uint64_t *look, Header *h) {
     constexpr int T = kDedupeThreads, IT = kDedupeItems, TILE = kDedupeTile, NW = T / 32;
     __shared__ uint64_t s_key[TILE + 1];
-    uint32_t *s_a = reinterpret_cast<uint32_t *>(s_key);  // reused once the flags are in registers
-    __shared__ uint32_t s_warp[NW + 1];
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_cnt[IT * NW];  // new-value count per (item row, warp), then offsets
+    __shared__ uint32_t s_tile, s_total;
     __shared__ int64_t s_excl;
 
     const uint64_t *keys = keys0;
@@ -35,45 +35,47 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
     const int valid = int(m - base < TILE ? m - base : TILE);
 
     // s_key[0] = predecessor of the tile, s_key[1 + i] = key[base + i]
+#pragma unroll 4
     for (int i = tid; i < valid; i += T) s_key[1 + i] = keys[base + i];
     if (tid == 0) s_key[0] = base > 0 ? keys[base - 1] : ~keys[0];
     __syncthreads();
 
-    uint32_t cnt = 0, flags = 0;
-    const int first = tid * IT;
+    // item (row j, warp w, lane) = j*T + w*32 + lane: striped, conflict-free
+    uint32_t masks[IT];
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
-        const int i = first + j;
-        if (i < valid && s_key[1 + i] != s_key[i]) {
-            ++cnt;
-            flags |= 1u << j;
-        }
+        const int i = j * T + tid;
+        const bool f = i < valid && s_key[1 + i] != s_key[i];
+        masks[j] = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_cnt[j * NW + warp] = __popc(masks[j]);
     }
-    // block exclusive scan of the per-thread counts
-    uint32_t inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < NW ? s_warp[lane] : 0u, wi = w;
+    if (warp == 0) {  // exclusive scan of the IT*NW counts, in item order
+        uint32_t c[IT * NW / 32], sum = 0;
+#pragma unroll
+        for (int q = 0; q < IT * NW / 32; ++q) {
+            c[q] = s_cnt[lane * (IT * NW / 32) + q];
+            sum += c[q];
+        }
+        uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        if (lane < NW) s_warp[lane] = wi - w;
-        if (lane == NW - 1) s_warp[NW] = wi;
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < IT * NW / 32; ++q) {
+            s_cnt[lane * (IT * NW / 32) + q] = run;
+            run += c[q];
+        }
+        if (lane == 31) s_total = inc;
     }
     __syncthreads();
-    const uint32_t texcl = inc - cnt + s_warp[warp];
-    const uint32_t total = s_warp[NW];
 
     // decoupled look-back on the tile totals
     if (tid == 0) {
+        const uint32_t total = s_total;
         uint64_t *my = look + tile;
         int64_t excl = 0;
         if (tile == 0) {
@@ -83,7 +85,7 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
             int64_t t = tile - 1;
             uint32_t spins = 0;
             while (t >= 0) {
-                uint64_t w = ld_volatile(look + t);
+                const uint64_t w = ld_volatile(look + t);
                 if ((w & kFlagMask) == 0) {
                     if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
                         set_status(h, PH0_ETIMEOUT);
@@ -103,17 +105,12 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
     }
     __syncthreads();
     const int64_t excl = s_excl;
-    uint32_t run = texcl;
+    const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
-        const int i = first + j;
-        if (i < valid) {
-            run += (flags >> j) & 1u;
-            s_a[i] = uint32_t(excl + run);
-        }
+        const int i = j * T + tid;
+        if (i < valid) a[base + i] = uint32_t(excl + s_cnt[j * NW + warp] + __popc(masks[j] & le));
     }
-    __syncthreads();
-    for (int i = tid; i < valid; i += T) a[base + i] = s_a[i];
 }
 
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,

@@ -17,8 +17,9 @@
 // run at 1/64 of the integer rate and the two pipes overlap; otherwise the
 // whole tile uses the binary64 units.
 //
-// Fused: the histogram of the low 8 key bits (radix pass 0), the min and max
-// key (the sort's bit range), and the finiteness check of the input.
+// Fused: the histograms of the six low 8-bit key digits (the low radix
+// passes), the min and max key (the sort's bit range), and the finiteness
+// check of the input.
 #include "emu64.cuh"
 #include "ph0_common.cuh"
 
@@ -64,7 +65,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     // [d][bt] u block, then [d][bt] v block: binary64 values, or int64 fixed
     // point in units of 2^g[k] on the integer path; then g[d], lo[d], hi[d]
     extern __shared__ double s_coord[];
-    __shared__ uint32_t s_hist[kRadix];
+    __shared__ uint32_t s_hist[kLowPasses][kRadix];
     __shared__ uint64_t s_min[kDistThreads / 32], s_max[kDistThreads / 32];
     __shared__ int s_fixed;
 
@@ -82,7 +83,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     int32_t *s_lo = s_g + d;
     int32_t *s_hi = s_lo + d;
 
-    for (int b = threadIdx.x; b < kRadix; b += blockDim.x) s_hist[b] = 0;
+    for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) (&s_hist[0][0])[b] = 0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
         s_lo[k] = 1 << 30;
         s_hi[k] = -(1 << 30);
@@ -151,7 +152,8 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
             int64_t e = edge_index(n, u, v);
             key[e] = kb;
             val[e] = (uint32_t(u) << 16) | uint32_t(v);
-            atomicAdd(&s_hist[kb & (kRadix - 1)], 1u);
+#pragma unroll
+            for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
             kmin = kb < kmin ? kb : kmin;
             kmax = kb > kmax ? kb : kmax;
         }
@@ -178,8 +180,10 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
             atomicMax((unsigned long long *)&h->kmax, (unsigned long long)kmax);
         }
     }
-    for (int b = threadIdx.x; b < kRadix; b += blockDim.x)
-        if (s_hist[b]) atomicAdd(&h->hist[0][b], s_hist[b]);
+    for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) {
+        const uint32_t c = (&s_hist[0][0])[b];
+        if (c) atomicAdd(&h->hist[b / kRadix][b % kRadix], c);
+    }
 }
 
 // Shared memory of a tile: two staged blocks plus g, lo, hi per dimension.

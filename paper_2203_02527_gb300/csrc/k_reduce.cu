@@ -313,37 +313,47 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         }
         if (tid == 0) s_hcount = 0;
         __syncthreads();
-        for (int64_t b = pos0 + int64_t(blockIdx.x) * kReduceThreads; b < wend; b += gstride) {
-            const int64_t p = b + tid;
-            bool direct = false;
-            if (p < wend) {
-                uint32_t vv = val[p];
-                if ((vv >> 16) >= n || (vv & 0xffffu) >= n) {  // corrupt input: never index past n
-                    set_status(h, PH0_EINTERNAL);
-                    vv = 0;
-                }
-                const uint32_t cu = s_comp[vv >> 16], cv = s_comp[vv & 0xffffu];
-                if (cu != cv) {
-                    const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
-                    const uint32_t pair = (lo << 16) | hi;
-                    bool done = false;
-                    if (*(volatile uint32_t *)&s_hcount < kHashSize / 2) {
-                        const uint32_t hs = (pair * 2654435761u) >> 21;  // 11 bits
-                        for (int pr = 0; pr < 8; ++pr) {
-                            const uint32_t slot = (hs + pr) & (kHashSize - 1);
-                            const uint32_t old = atomicCAS(&s_hkey[slot], kEmpty, pair);
-                            if (old == kEmpty) atomicAdd(&s_hcount, 1u);
-                            if (old == kEmpty || old == pair) {
-                                atomicMin(&s_hval[slot], uint32_t(p));
-                                done = true;
-                                break;
+        // four loads in flight per thread and iteration
+        for (int64_t b = pos0 + int64_t(blockIdx.x) * (4 * kReduceThreads); b < wend; b += 4 * gstride) {
+            uint32_t vq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t p = b + q * kReduceThreads + tid;
+                vq[q] = p < wend ? val[p] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t p = b + q * kReduceThreads + tid;
+                bool direct = false;
+                if (p < wend) {
+                    uint32_t vv = vq[q];
+                    if ((vv >> 16) >= n || (vv & 0xffffu) >= n) {  // corrupt input: never index past n
+                        set_status(h, PH0_EINTERNAL);
+                        vv = 0;
+                    }
+                    const uint32_t cu = s_comp[vv >> 16], cv = s_comp[vv & 0xffffu];
+                    if (cu != cv) {
+                        const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
+                        const uint32_t pair = (lo << 16) | hi;
+                        bool done = false;
+                        if (*(volatile uint32_t *)&s_hcount < kHashSize / 2) {
+                            const uint32_t hs = (pair * 2654435761u) >> 21;  // 11 bits
+                            for (int pr = 0; pr < 8; ++pr) {
+                                const uint32_t slot = (hs + pr) & (kHashSize - 1);
+                                const uint32_t old = atomicCAS(&s_hkey[slot], kEmpty, pair);
+                                if (old == kEmpty) atomicAdd(&s_hcount, 1u);
+                                if (old == kEmpty || old == pair) {
+                                    atomicMin(&s_hval[slot], uint32_t(p));
+                                    done = true;
+                                    break;
+                                }
                             }
                         }
+                        direct = !done;
                     }
-                    direct = !done;
                 }
+                warp_append(direct, uint32_t(p), A.cand0, &h->nlist[0]);
             }
-            warp_append(direct, uint32_t(p), A.cand0, &h->nlist[0]);
         }
         __syncthreads();
         for (int slot = tid; slot < kHashSize; slot += kReduceThreads) {

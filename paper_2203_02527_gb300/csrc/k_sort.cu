@@ -62,24 +62,25 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words) {
         h->sort_passes = 0;
         h->key_bits = 0;
     }
-    for (int64_t i = tid; i < int64_t(kMaxPasses) * kRadix; i += stride)
+    for (int64_t i = tid; i < int64_t(kMaxPasses) * kMaxRadix; i += stride)
         (&h->hist[0][0])[i] = 0;
     for (int64_t i = tid; i < kMaxPasses + 4; i += stride) h->tile_counter[i] = 0;
     for (int64_t i = tid; i < look_words; i += stride) look0[i] = 0;
 }
 
-// Pass-0 histogram (raw low 8 bits) and key range of keys not produced by
+// Histograms of the six low digits and the key range of keys not produced by
 // the distance kernel (which computes both itself).
 __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ keys, int64_t m, Header *h) {
-    __shared__ uint32_t s_hist[kRadix];
+    __shared__ uint32_t s_hist[kLowPasses][kRadix];
     __shared__ uint64_t s_min[8], s_max[8];
-    s_hist[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kLowPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     uint64_t kmin = ~0ull, kmax = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += int64_t(gridDim.x) * blockDim.x) {
-        uint64_t k = keys[i];
-        atomicAdd(&s_hist[k & (kRadix - 1)], 1u);
+        const uint64_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < kLowPasses; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & (kRadix - 1)], 1u);
         kmin = k < kmin ? k : kmin;
         kmax = k > kmax ? k : kmax;
     }
@@ -104,140 +105,299 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
             atomicMax((unsigned long long *)&h->kmax, (unsigned long long)kmax);
         }
     }
-    if (s_hist[threadIdx.x]) atomicAdd(&h->hist[0][threadIdx.x], s_hist[threadIdx.x]);
+    for (int i = threadIdx.x; i < kLowPasses * kRadix; i += blockDim.x) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&h->hist[i / kRadix][i % kRadix], c);
+    }
 }
 
-// One radix pass.  Pass p reads buffer p&1 and writes buffer (p+1)&1; its
-// look-back words live in look[p&1], and it clears its tile's words in
+// Shared memory of one pass: the tile's keys (input, then in sorted order),
+// its values (input, and in sorted order), per-warp digit counts, per-digit
+// destination offsets.
+template <int RADIX>
+struct SortSmem {
+    static constexpr int W = kSortThreads / 32;
+    uint64_t keys[kSortTile];          // input keys, then the tile's keys in sorted order
+    uint32_t vals_in[kSortTile];       // input values
+    uint32_t vals[kSortTile];          // values in sorted order
+    uint16_t whist[W][RADIX];          // counts, then exclusive warp offsets
+    int64_t gofs[RADIX];               // global position of sorted tile index 0 of each digit's run
+    uint32_t lstart[RADIX];            // local start of each digit in the tile
+    uint32_t next[kMaxRadix];          // histogram(s) of the top digit(s) (last low pass only)
+    uint32_t scan[W + 1];
+    uint32_t tile;
+    unsigned long long mbar;           // completion of the tile's bulk copies
+};
+
+// ---- bulk (TMA) copies global -> shared with an mbarrier -------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared, 16-byte aligned addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Bounded wait for phase `parity` of the barrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Digit of a key in pass slot SLOT: slots 0..5 are the raw bytes of bits
+// 0..47; slot 6 is the top part (all of it if it has at most 9 bits, else its
+// low byte); slot 7 is the high byte of a 16-bit top part.
+template <int SLOT>
+__device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p) {
+    if (SLOT < kLowPasses) return uint32_t(key >> (kRadixBits * SLOT)) & (kRadix - 1);
+    const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+    if (SLOT == kLowPasses) return p.top == 1 ? t : (t & (kRadix - 1));
+    return t >> kRadixBits;
+}
+
+// Decoupled look-back for one digit (column `col` of the per-tile status
+// words, stride kMaxRadix): the sum of the counts of all tiles before `tile`.
+// The PREFIX of the nearest finished predecessor typically lies tens of tiles
+// back, so kLookWindow predecessors are read at once and folded in order;
+// waits on unpublished words are bounded.
+#ifndef PH0_LOOK_WINDOW
+#define PH0_LOOK_WINDOW 16
+#endif
+constexpr int kLookWindow = PH0_LOOK_WINDOW;
+__device__ __forceinline__ int64_t lookback_window(const uint64_t *col, int64_t tile, Header *h) {
+    int64_t excl = 0;
+    int64_t t = tile - 1;  // next predecessor to fold
+    uint32_t spins = 0;
+    while (t >= 0) {
+        uint64_t w[kLookWindow];
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) w[q] = t - q >= 0 ? ld_volatile(col + (t - q) * kMaxRadix) : 0;
+        bool done = false, blocked = false;
+        int folded = 0;
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) {  // unrolled: w stays in registers
+            if (!done && !blocked && t - q >= 0) {
+                const uint64_t f = w[q] & kFlagMask;
+                if (f == 0) {
+                    blocked = true;  // not published yet: reload from here
+                } else {
+                    excl += int64_t(w[q] & kCountMask);
+                    ++folded;
+                    done = f == kFlagPrefix;
+                }
+            }
+        }
+        if (done) break;
+        t -= folded;
+        if (blocked) {
+            if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
+                set_status(h, PH0_ETIMEOUT);
+                break;
+            }
+            if (spins > 32) __nanosleep(64);
+        }
+    }
+    return excl;
+}
+
+#ifndef PH0_SORT_MIN_BLOCKS
+#define PH0_SORT_MIN_BLOCKS 3
+#endif
+
+// One radix pass (pass index = SLOT).  Pass p reads buffer p&1 and writes
+// buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
+// pass's radix) live in look[p&1], and it clears its tile's words in
 // look[(p+1)&1] for the next pass (whose previous user, pass p-1, is done).
-__global__ void __launch_bounds__(kSortThreads)
-k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m, int pass,
+template <int RADIX, int SLOT>
+__global__ void __launch_bounds__(kSortThreads, PH0_SORT_MIN_BLOCKS)
+k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
            uint64_t *look0, uint64_t *look1, Header *h) {
-    constexpr int THREADS = kSortThreads, ITEMS = kSortItems, TILE = kSortTile;
-    constexpr int WARPS = THREADS / 32;
-    static_assert(THREADS == kRadix, "one look-back thread per digit");
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(s_dyn);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_dyn + sizeof(uint64_t) * TILE);
-    __shared__ uint32_t s_whist[WARPS][kRadix];
-    __shared__ uint32_t s_lstart[kRadix];
-    __shared__ int64_t s_gbase[kRadix];
-    __shared__ uint32_t s_next[kRadix];
-    __shared__ uint32_t s_scan[WARPS + 1];
-    __shared__ uint32_t s_tile;
+    constexpr int T = kSortThreads, IT = kSortItems, TILE = kSortTile, W = T / 32;
+    constexpr int DPT = RADIX / T;  // digits per thread
+    static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    SortSmem<RADIX> &S = *reinterpret_cast<SortSmem<RADIX> *>(s_raw);
 
     const Plan plan = make_plan(h->kmin, h->kmax);
-    if (pass >= plan.passes) return;
-    const uint64_t *kin = (pass & 1) ? keys1 : keys0;
-    uint64_t *kout = (pass & 1) ? keys0 : keys1;
-    const uint32_t *vin = (pass & 1) ? vals1 : vals0;
-    uint32_t *vout = (pass & 1) ? vals0 : vals1;
-    uint64_t *look = (pass & 1) ? look1 : look0;
-    uint64_t *look_next = (pass & 1) ? look0 : look1;
-    const bool hist_next = pass + 1 < plan.passes;
+    if (SLOT >= plan.passes) return;
+    const uint64_t *kin = (SLOT & 1) ? keys1 : keys0;
+    uint64_t *kout = (SLOT & 1) ? keys0 : keys1;
+    const uint32_t *vin = (SLOT & 1) ? vals1 : vals0;
+    uint32_t *vout = (SLOT & 1) ? vals0 : vals1;
+    uint64_t *look = (SLOT & 1) ? look1 : look0;
+    uint64_t *look_next = (SLOT & 1) ? look0 : look1;
+    const bool hist_top = plan.top > 0 && SLOT == plan.low - 1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&h->tile_counter[pass], 1u);
-    for (int w = 0; w < WARPS; ++w) s_whist[w][tid] = 0;
-    s_next[tid] = 0;
-    // bucket start of digit `tid`: exclusive scan of this pass's histogram
-    uint32_t total_all;
-    const uint32_t bucket = block_excl_scan<THREADS>(h->hist[pass][tid], s_scan, total_all);
-    const int64_t tile = s_tile;
+    if (tid == 0) {
+        S.tile = atomicAdd(&h->tile_counter[SLOT], 1u);
+        mbar_init(&S.mbar, 1);
+    }
+    __syncthreads();
+    const int64_t tile = S.tile;
     const int64_t base = tile * TILE;
-
-    // ---- load (striped within each warp: coalesced) and rank stably ----
-    uint64_t k[ITEMS];
-    uint32_t v[ITEMS], rank[ITEMS], dig[ITEMS];
-    const int64_t wbase = base + int64_t(warp) * 32 * ITEMS;
+    const int valid = int(m - base < TILE ? m - base : TILE);
+    // full tiles with 16-byte aligned rows arrive by two bulk copies that
+    // overlap the histogram scan below; the ragged last tile uses plain loads
+    const bool bulk = valid == TILE &&
+                      ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15u) == 0;
+    if (bulk && tid == 0) {
+        mbar_expect_tx(&S.mbar, uint32_t(TILE * (sizeof(uint64_t) + sizeof(uint32_t))));
+        bulk_g2s(S.keys, kin + base, uint32_t(TILE * sizeof(uint64_t)), &S.mbar);
+        bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
+    }
+    for (int i = tid; i < W * RADIX / 2; i += T) reinterpret_cast<uint32_t *>(&S.whist[0][0])[i] = 0;
+    if (hist_top)
+        for (int i = tid; i < kMaxRadix; i += T) S.next[i] = 0;
+    // bucket starts: exclusive scan of this pass's histogram (thread owns DPT digits)
+    uint32_t bucket[DPT], hsum = 0;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int64_t idx = wbase + j * 32 + lane;
-        const bool ok = idx < m;
-        k[j] = ok ? kin[idx] : 0;
-        v[j] = ok ? vin[idx] : 0;
-        dig[j] = ok ? digit_of(k[j], plan, pass) : uint32_t(kRadix);
+    for (int q = 0; q < DPT; ++q) {
+        bucket[q] = h->hist[SLOT][tid * DPT + q];
+        hsum += bucket[q];
+    }
+    {
+        uint32_t tot;
+        uint32_t run = block_excl_scan<T>(hsum, S.scan, tot);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const uint32_t c = bucket[q];
+            bucket[q] = run;
+            run += c;
+        }
+    }
+
+    // ---- keys (striped within each warp) and stable ranking ----
+    uint64_t k[IT];
+    uint32_t dr[IT];  // digit << 16 | rank within the warp, then the local position
+    const int wloc = warp * 32 * IT;  // the warp's first item within the tile
+    if (bulk) {
+        if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
+#pragma unroll
+        for (int j = 0; j < IT; ++j) k[j] = S.keys[wloc + j * 32 + lane];
+    } else {
+#pragma unroll
+        for (int j = 0; j < IT; ++j) {
+            const int loc = wloc + j * 32 + lane;
+            k[j] = loc < valid ? kin[base + loc] : 0;
+        }
     }
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t dj = dig[j];
+    for (int j = 0; j < IT; ++j) {
+        const uint32_t dj = (bulk || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan)
+                                                                   : uint32_t(RADIX);
         const unsigned peers = __match_any_sync(0xffffffffu, dj);
         const uint32_t before = __popc(peers & lt);
-        const uint32_t cnt = __popc(peers);
-        const uint32_t prior = dj < kRadix ? s_whist[warp][dj] : 0u;
-        rank[j] = prior + before;
+        const uint32_t prior = dj < RADIX ? S.whist[warp][dj] : 0u;
+        dr[j] = (dj << 16) | (prior + before);
         __syncwarp();
-        if (dj < kRadix && before == 0) s_whist[warp][dj] = prior + cnt;
+        if (dj < RADIX && before == 0) S.whist[warp][dj] = uint16_t(prior + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
 
-    // ---- per-digit tile totals and warp offsets (thread tid = digit) ----
-    uint32_t total = 0;
-    for (int w = 0; w < WARPS; ++w) {
-        uint32_t c = s_whist[w][tid];
-        s_whist[w][tid] = total;
-        total += c;
-    }
-    // ---- decoupled look-back for digit tid ----
-    uint64_t *my = look + tile * kRadix + tid;
-    int64_t excl = 0;
-    if (tile == 0) {
-        st_volatile(my, kFlagPrefix | total);
-    } else {
-        st_volatile(my, kFlagAgg | total);
-        int64_t t = tile - 1;
-        uint32_t spins = 0;
-        while (t >= 0) {
-            uint64_t w = ld_volatile(look + t * kRadix + tid);
-            if ((w & kFlagMask) == 0) {
-                if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
-                    set_status(h, PH0_ETIMEOUT);
-                    break;
-                }
-                if (spins > 32) __nanosleep(64);
-                continue;
-            }
-            excl += int64_t(w & kCountMask);
-            if ((w & kFlagMask) == kFlagPrefix) break;
-            --t;
-        }
-        st_volatile(my, kFlagPrefix | uint64_t(excl + total));
-    }
-    s_gbase[tid] = int64_t(bucket) + excl;
-    uint32_t tile_total;
-    s_lstart[tid] = block_excl_scan<THREADS>(total, s_scan, tile_total);
-    __syncthreads();
-
-    // ---- reorder the tile by digit in shared memory ----
+    // ---- per digit: warp offsets and tile total; publish the total at once ----
+    uint32_t total[DPT], tsum = 0;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t dj = dig[j];
-        if (dj < kRadix) {
-            const uint32_t pos = s_lstart[dj] + s_whist[warp][dj] + rank[j];
-            s_keys[pos] = k[j];
-            s_vals[pos] = v[j];
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t c = S.whist[w][d];
+            S.whist[w][d] = uint16_t(t);
+            t += c;
+        }
+        total[q] = t;
+        tsum += t;
+        st_volatile(look + tile * kMaxRadix + d, (tile == 0 ? kFlagPrefix : kFlagAgg) | t);
+    }
+    {
+        uint32_t tot;
+        uint32_t run = block_excl_scan<T>(tsum, S.scan, tot);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            S.lstart[tid * DPT + q] = run;
+            run += total[q];
         }
     }
     __syncthreads();
 
-    // ---- write contiguous runs; histogram the next digit ----
-    const int valid = int(m - base < TILE ? m - base : TILE);
-    for (int i = tid; i < valid; i += THREADS) {
-        const uint64_t key = s_keys[i];
-        const uint32_t d = digit_of(key, plan, pass);
-        const int64_t g = s_gbase[d] + (i - int64_t(s_lstart[d]));
-        kout[g] = key;
-        vout[g] = s_vals[i];
-        if (hist_next) atomicAdd(&s_next[digit_of(key, plan, pass + 1)], 1u);
+    // ---- reorder keys and values by digit in shared memory ----
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const uint32_t dj = dr[j] >> 16;
+        const int loc = wloc + j * 32 + lane;
+        if (dj < RADIX) {
+            const uint32_t pos = S.lstart[dj] + S.whist[warp][dj] + (dr[j] & 0xffffu);
+            S.keys[pos] = k[j];
+            S.vals[pos] = bulk ? S.vals_in[loc] : vin[base + loc];
+        }
     }
-    look_next[tile * kRadix + tid] = 0;
+
+    // ---- look-back (keys and ranks are dead now), global offsets ----
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        int64_t excl = 0;
+        if (tile != 0) {
+            excl = lookback_window(look + d, tile, h);
+            st_volatile(look + tile * kMaxRadix + d, kFlagPrefix | uint64_t(excl + total[q]));
+        }
+        S.gofs[d] = int64_t(bucket[q]) + excl - int64_t(S.lstart[d]);
+    }
     __syncthreads();
-    if (hist_next && s_next[tid]) atomicAdd(&h->hist[pass + 1][tid], s_next[tid]);
+
+    // ---- write contiguous runs, one per digit ----
+#pragma unroll 4
+    for (int i = tid; i < valid; i += T) {
+        const uint64_t key = S.keys[i];
+        const int64_t g = S.gofs[slot_digit<SLOT>(key, plan)] + i;
+        kout[g] = key;
+        vout[g] = S.vals[i];
+        if (hist_top) {
+            const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
+            if (plan.top == 1) {
+                atomicAdd(&S.next[t], 1u);
+            } else {  // two top passes: low and high byte of t
+                atomicAdd(&S.next[t & (kRadix - 1)], 1u);
+                atomicAdd(&S.next[kRadix + (t >> kRadixBits)], 1u);
+            }
+        }
+    }
+    for (int i = tid; i < kMaxRadix; i += T) look_next[tile * kMaxRadix + i] = 0;
+    if (hist_top) {
+        __syncthreads();
+        for (int i = tid; i < kMaxRadix; i += T) {
+            const uint32_t c = S.next[i];
+            if (!c) continue;
+            if (plan.top == 1) atomicAdd(&h->hist[SLOT + 1][i], c);
+            else atomicAdd(&h->hist[SLOT + 1 + i / kRadix][i % kRadix], c);
+        }
+    }
     if (tile == 0 && tid == 0) {
         h->sort_passes = plan.passes;
-        h->key_bits = plan.nbits;
+        h->key_bits = plan.bits;
     }
 }
 
@@ -255,7 +415,8 @@ __global__ void k_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *
 }
 
 // ------------------------------------------------------------------ host ---
-constexpr size_t kSortDynSmem = size_t(kSortTile) * (sizeof(uint64_t) + sizeof(uint32_t));
+template <int RADIX>
+constexpr size_t sort_smem() { return sizeof(SortSmem<RADIX>); }
 
 int sm_count() {
     int dev = 0, sms = 0;
@@ -264,9 +425,9 @@ int sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-// Zero the sort's counters and first look-back buffer.
+// Zero the sort's counters and first look-back buffer (sized for 512 buckets).
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s) {
-    const int64_t words = tiles * kRadix;
+    const int64_t words = tiles * kMaxRadix;
     int blocks = int((words + 255) / 256);
     if (blocks < 8) blocks = 8;
     if (blocks > 4 * sm_count() * 8) blocks = 4 * sm_count() * 8;
@@ -283,36 +444,63 @@ cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStre
     return cudaGetLastError();
 }
 
+template <int RADIX, int SLOT>
+static cudaError_t set_attr() {
+    return cudaFuncSetAttribute(k_onesweep<RADIX, SLOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sort_smem<RADIX>()));
+}
+
+cudaError_t prepare_sort_kernels() {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = set_attr<kRadix, 0>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 1>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 2>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 3>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 4>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 5>();
+    if (e == cudaSuccess) e = set_attr<kMaxRadix, 6>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 7>();
+    return e;
+}
+
+template <int RADIX, int SLOT>
+static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                        int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s) {
+    k_onesweep<RADIX, SLOT><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1, m,
+                                                                             look0, look1, h);
+}
+
+// One pass slot (prepare_sort_kernels() must have run).
+cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                             int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
+                             cudaStream_t s) {
+    const unsigned tiles = unsigned((m + kSortTile - 1) / kSortTile);
+    switch (pass) {
+        case 0: launch_slot<kRadix, 0>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 1: launch_slot<kRadix, 1>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 2: launch_slot<kRadix, 2>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 3: launch_slot<kRadix, 3>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 4: launch_slot<kRadix, 4>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 5: launch_slot<kRadix, 5>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 6: launch_slot<kMaxRadix, 6>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        default: launch_slot<kRadix, 7>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+    }
+    return cudaGetLastError();
+}
+
 // The passes over buffers (keys0, vals0) <-> (keys1, vals1); the sorted data
 // ends in buffer (passes & 1), which the device records in the header.
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
                                cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(kSortDynSmem));
+    cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (m + kSortTile - 1) / kSortTile;
     for (int p = 0; p < kMaxPasses; ++p) {
-        k_onesweep<<<unsigned(tiles), kSortThreads, kSortDynSmem, s>>>(keys0, keys1, vals0, vals1, m, p,
-                                                                        look0, look1, h);
-        e = cudaGetLastError();
+        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-const void *k_onesweep_symbol() { return (const void *)k_onesweep; }
-size_t sort_dyn_smem() { return kSortDynSmem; }
-
-// One pass (the attribute for the dynamic shared memory must be set).
-cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                             int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
-                             cudaStream_t s) {
-    const int64_t tiles = (m + kSortTile - 1) / kSortTile;
-    k_onesweep<<<unsigned(tiles), kSortThreads, kSortDynSmem, s>>>(keys0, keys1, vals0, vals1, m, pass,
-                                                                    look0, look1, h);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,

@@ -20,8 +20,7 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
 cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                              int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
                              cudaStream_t s);
-const void *k_onesweep_symbol();
-size_t sort_dyn_smem();
+cudaError_t prepare_sort_kernels();
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
@@ -200,9 +199,7 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     if (e == cudaSuccess) e = begin_call(ws, L, s);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
-    if (e == cudaSuccess && L.m > 0)
-        e = cudaFuncSetAttribute(k_onesweep_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(sort_dyn_smem()));
+    if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
         if (L.m > 0) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);

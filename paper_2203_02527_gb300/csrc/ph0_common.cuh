@@ -15,9 +15,12 @@ namespace ph0 {
 // ---------------------------------------------------------------- limits ---
 constexpr int64_t kMaxN = 65535;   // vertex ids packed in 16 bits: E < 2^31
 constexpr int32_t kMaxD = 1024;
-constexpr int kMaxPasses = 8;      // 64-bit keys, digits of at most 8 bits
+constexpr int kMaxPasses = 8;      // 6 low digit passes + at most 2 top passes
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kLowPasses = 6;      // raw 8-bit digits of key bits 0..47
+constexpr int kTopShift = 48;      // the rest, key >> 48, is sorted offset by kmin >> 48
+constexpr int kMaxRadix = 512;     // one top pass of up to 9 bits
 
 // Bounded device-side waits: about a second at most, then the kernel records
 // PH0_ETIMEOUT in the status word and returns cleanly.
@@ -58,10 +61,10 @@ struct Header {
     uint32_t npiv;               // pivots claimed so far
     uint32_t nlist[2];           // candidate list lengths (ping-pong)
     uint32_t pad[6];
-    uint32_t hist[kMaxPasses][kRadix];  // digit histogram per radix pass
+    uint32_t hist[kMaxPasses][kMaxRadix];  // digit histogram per radix pass
 };
 
-constexpr size_t kHeaderBytes = 16384;
+constexpr size_t kHeaderBytes = 32768;
 static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) {
@@ -112,8 +115,8 @@ struct Layout {
         val[0] = take(4 * size_t(m));
         val[1] = take(4 * size_t(m));
         a = take(4 * size_t(m));
-        look[0] = take(8 * size_t(tiles) * kRadix);
-        look[1] = take(8 * size_t(tiles) * kRadix);
+        look[0] = take(8 * size_t(tiles) * kMaxRadix);
+        look[1] = take(8 * size_t(tiles) * kMaxRadix);
         dlook = take(8 * size_t(tiles + 1));
         comp = take(4 * size_t(n));
         parent = take(4 * size_t(n));
@@ -125,8 +128,8 @@ struct Layout {
         kill_key[1] = take(8 * size_t(n));
         kill_val[0] = take(4 * size_t(n));
         kill_val[1] = take(4 * size_t(n));
-        kill_look[0] = take(8 * size_t(ktiles) * kRadix);
-        kill_look[1] = take(8 * size_t(ktiles) * kRadix);
+        kill_look[0] = take(8 * size_t(ktiles) * kMaxRadix);
+        kill_look[1] = take(8 * size_t(ktiles) * kMaxRadix);
         grad = take(8 * size_t(n) * size_t(d_ > 0 ? d_ : 1));
         trace = take(sizeof(uint64_t) * kTraceWords * kTraceWindows);
         total = off;
@@ -178,25 +181,48 @@ __host__ __device__ __forceinline__ int64_t edge_index(int64_t n, int64_t u, int
     return u * (2 * n - u - 1) / 2 + (v - u - 1);
 }
 
-// Radix plan.  Pass 0 sorts the raw low 8 bits (its histogram is taken where
-// the keys are produced, before kmin is known); the other passes sort 8-bit
-// digits of (key - kbase), kbase = kmin with its low 8 bits cleared, which
-// leaves the low digit unchanged and drops the constant high bits.
+// Radix plan.  Bits above the highest bit in which the keys differ are
+// constant and not sorted.  The low passes sort raw 8-bit digits of bits
+// 0..47, whose histograms can be taken where the keys are produced (before
+// the key range is known).  If the keys differ above bit 47, the top part
+// T = (key >> 48) - (kmin >> 48) (in key order, since the offset is constant)
+// is sorted last: in one pass of up to 9 bits (512 buckets) or in two passes
+// of 8 bits; its histograms are taken during the last low pass.
 struct Plan {
-    uint64_t kbase;
-    int nbits, passes;
+    uint64_t kmin;
+    int low, top, passes, bits;
 };
-__device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax) {
+__host__ __device__ __forceinline__ int bitlen64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return x ? 64 - __clzll((long long)x) : 0;
+#else
+    return x ? 64 - __builtin_clzll(x) : 0;
+#endif
+}
+__host__ __device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax) {
     Plan p;
-    p.kbase = kmin & ~uint64_t(kRadix - 1);
-    uint64_t span = kmax > p.kbase ? kmax - p.kbase : 0;
-    p.nbits = span ? 64 - __clzll((long long)span) : 0;
-    p.passes = p.nbits <= kRadixBits ? 1 : 1 + (p.nbits - kRadixBits + kRadixBits - 1) / kRadixBits;
+    p.kmin = kmin;
+    if (kmax < kmin) kmax = kmin;  // no keys
+    const int hi = bitlen64(kmin ^ kmax);
+    if (hi <= kTopShift) {
+        p.low = (hi + kRadixBits - 1) / kRadixBits;
+        p.top = 0;
+        p.bits = hi;
+    } else {
+        const int tb = bitlen64((kmax >> kTopShift) - (kmin >> kTopShift));
+        p.low = kLowPasses;
+        p.top = tb <= 9 ? 1 : 2;
+        p.bits = kTopShift + tb;
+    }
+    p.passes = p.low + p.top;
     return p;
 }
-__device__ __forceinline__ uint32_t digit_of(uint64_t key, const Plan &p, int pass) {
-    if (pass == 0) return uint32_t(key) & (kRadix - 1);
-    return uint32_t((key - p.kbase) >> (kRadixBits * pass)) & (kRadix - 1);
+// Digit of a key in a pass (< 512 in a single top pass, else < 256).
+__host__ __device__ __forceinline__ uint32_t digit_of(uint64_t key, const Plan &p, int pass) {
+    if (pass < p.low) return uint32_t(key >> (kRadixBits * pass)) & (kRadix - 1);
+    const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+    if (p.top == 1) return t;
+    return pass == p.low ? (t & (kRadix - 1)) : (t >> kRadixBits);
 }
 
 }  // namespace ph0
