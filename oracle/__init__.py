@@ -205,6 +205,19 @@ def death_gradient(x64, bar_u, bar_v, dl_ddeath):
     return out
 
 
+def barcodes_f64(x64):
+    """Bars of binary64 points (for finite differences): (order, u, v, d2)
+    of the killing edges in filtration order."""
+    x64 = np.ascontiguousarray(np.asarray(x64, np.float64))
+    n = len(x64)
+    u, v = edge_endpoints(n)
+    d2 = distances_f64(x64)
+    order = sort_edges(d2, u, v)
+    low, _, _ = reduce(n, u[order], v[order])
+    piv = np.flatnonzero(low >= 0)
+    return order[piv], u[order][piv], v[order][piv], d2[order][piv]
+
+
 def pipeline(x):
     """Every intermediate of the path, for step-by-step parity tests:
     dict with d2 (edge id order), order, sorted u/v/d2, a, |D|, low, bars."""

@@ -210,3 +210,30 @@ def backward(pts: torch.Tensor, bars: Bars, dl_ddeath: torch.Tensor,
                                             _ptr(grad), ws.ptr, ws.nbytes, _stream()),
           "ph0_barcodes_backward")
     return grad
+
+
+# ------------------------------------------------------------ autograd ---
+
+class DeathValues(torch.autograd.Function):
+    """death_i = distance of the i-th killing edge (filtration order), as a
+    differentiable function of the points.  The pairing (which edges kill) is
+    piecewise constant in the points, so the derivative is that of the
+    killing edges' lengths; the backward pass is the hand-written kernel."""
+
+    @staticmethod
+    def forward(ctx, pts, ws=None):
+        bars = barcodes(pts, ws)
+        ctx.save_for_backward(pts)
+        ctx.bars = bars
+        ctx.ws = ws
+        return bars.death
+
+    @staticmethod
+    def backward(ctx, grad_death):
+        (pts,) = ctx.saved_tensors
+        return backward(pts, ctx.bars, grad_death, ctx.ws), None
+
+
+def death_values(pts: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor:
+    """Finite death values (float64 [N-1], filtration order), differentiable."""
+    return DeathValues.apply(pts, ws)
