@@ -194,6 +194,57 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
 int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                          ph0_bar *bars_dev, void *stream);
 
+/* ---- serving: a context that admits clouds as they arrive ----
+ *
+ * The paper computes one cloud at a time (Sec. 3.1, Sec. 4.1); this context
+ * (no counterpart in the paper) keeps several clouds of any N and d on the GPU
+ * at once.  It allocates one device arena (mem_budget) and one pinned host
+ * pool (host_budget) when created, owns a worker thread, and admits queued
+ * clouds in arrival order whenever their buffers fit and a slot is free.  Large
+ * clouds run the same kernels as ph0_barcodes, each on its own stream; clouds
+ * with n <= small_max_n (and d <= 64) are grouped into one launch of a fused
+ * kernel that computes each cloud in one CTA (replayed from a captured CUDA
+ * graph).  Every result equals what ph0_barcodes returns for that cloud. */
+typedef struct ph0_ctx ph0_ctx;
+
+typedef struct {
+    size_t mem_budget;    /* device bytes for all clouds in flight (>= 1 MiB)       */
+    size_t host_budget;   /* pinned host bytes for queued points and finished bars */
+    int32_t streams;      /* large clouds in flight at once (1..64)                 */
+    int32_t small_max_n;  /* batch clouds with n <= this (<= 180; 0 = never)        */
+    int32_t batch_max;    /* clouds per fused launch                                */
+    int32_t reserved;
+} ph0_options;
+
+typedef struct {
+    uint64_t tag;         /* as submitted                                           */
+    int32_t status;       /* ph0_status of this cloud                               */
+    int32_t n, d;
+    int32_t reserved;
+    int64_t n_bars;       /* n - 1                                                  */
+    const ph0_bar *bars;  /* host memory owned by the context until ph0_release     */
+    double submit_time;   /* steady-clock seconds at ph0_submit                     */
+    double done_time;     /* steady-clock seconds when the worker saw it complete   */
+} ph0_result;
+
+/* Creates a context on the current device.  Returns PH0_ECUDA if the arena or
+ * pool cannot be allocated. */
+int ph0_ctx_create(const ph0_options *opt, ph0_ctx **ctx);
+
+/* Queues a cloud (points copied from host memory at once, float32 [n, d]).
+ * PH0_EBUSY: the host pool is full (poll and release first); PH0_ENOMEM: the
+ * cloud can never fit mem_budget; PH0_EINVAL: the tag is still in use. */
+int ph0_submit(ph0_ctx *ctx, const float *pts_host, int64_t n, int32_t d, uint64_t tag);
+
+/* Returns up to `max` finished clouds (waiting up to wait_ms if none). */
+int ph0_poll(ph0_ctx *ctx, ph0_result *out, int32_t max, int32_t *got, int32_t wait_ms);
+
+/* Frees a returned result's host memory; the tag may then be reused. */
+int ph0_release(ph0_ctx *ctx, uint64_t tag);
+
+/* Waits for the work in flight and frees everything. */
+int ph0_ctx_destroy(ph0_ctx *ctx);
+
 /* ---- differentiation ---- */
 
 /* Backward of death_i = |x_v - x_u| for fixed killing edges:

@@ -62,6 +62,23 @@ class Profile(ctypes.Structure):
         return d
 
 
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("mem_budget", ctypes.c_size_t), ("host_budget", ctypes.c_size_t),
+        ("streams", ctypes.c_int32), ("small_max_n", ctypes.c_int32),
+        ("batch_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_int32),
+        ("d", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_bars", ctypes.c_int64),
+        ("bars", ctypes.c_void_p), ("submit_time", ctypes.c_double),
+        ("done_time", ctypes.c_double),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -79,6 +96,11 @@ SIGNATURES = {
     "ph0_trace_windows": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32]),
     "ph0_barcodes_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP]),
     "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
+    "ph0_ctx_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.POINTER(_VP)]),
+    "ph0_submit": (ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.c_uint64]),
+    "ph0_poll": (ctypes.c_int, [_VP, ctypes.POINTER(Result), _I32, ctypes.POINTER(_I32), _I32]),
+    "ph0_release": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "ph0_ctx_destroy": (ctypes.c_int, [_VP]),
     "ph0_sort": (ctypes.c_int, [_VP, _VP, _I64, _VP, _SZ, _VP]),
     "ph0_dedupe": (ctypes.c_int, [_VP, _I64, _VP, _VP, _SZ, _VP]),
     "ph0_reduce": (ctypes.c_int, [_I64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),

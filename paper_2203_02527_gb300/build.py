@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     print(out)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -512,7 +512,10 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (per_sm > 2) per_sm = 2;
-    const int grid = sm_count() * per_sm;
+    // small clouds: fewer CTAs (cheaper grid barriers; other clouds may share the GPU)
+    int grid = sm_count() * per_sm;
+    const int64_t want = (A.n + 63) / 64;
+    if (want < grid) grid = want < 4 ? 4 : int(want);
     ReduceArgs args = A;
     void *params[] = {&args};
     return cudaLaunchCooperativeKernel((const void *)k_reduce, dim3(grid), dim3(kReduceThreads), params,

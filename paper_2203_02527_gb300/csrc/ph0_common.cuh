@@ -153,6 +153,15 @@ struct ReduceArgs {
     uint64_t *trace;               // [kTraceWindows][kTraceWords]
 };
 
+// One cloud of a fused small-cloud batch (k_small.cu).
+struct SmallTask {
+    const float *pts;      // device [n, ld]
+    int64_t *fixed;        // device scratch [n * d] int64 (fixed-point coordinates)
+    ph0_bar *bars;         // device [n - 1]
+    int32_t *status;       // device, one word per task
+    int32_t n, d, ld, pad;
+};
+
 template <typename T>
 __host__ __device__ inline T *at(void *ws, size_t off) {
     return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
