@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 from paper_2203_02527_gb300 import inputs  # noqa: E402
 
 WORKLOAD = "circles32768"
+# DRAM bytes per edge of one low radix pass (dram__bytes_read.sum +
+# dram__bytes_write.sum of k_onesweep<256, 0..3> on the 8192-point cloud,
+# profiles/kernels_circles8192.md), scaled by edges to a full launch.
+ONESWEEP_TRAFFIC_PER_EDGE = 23.96
 METRIC = "edges sorted+reduced/s at N=32768"
 # bounded sample of the workload for the CPU oracle: every 5th point
 SAMPLE_STRIDE = 5
@@ -245,8 +249,10 @@ def run_ours(args, rank, world, local_rank):
     else:
         achieved = 24.0 * m / (per_pass_ms * 1e-3) / 1e9
         roof = {"kernel": "k_onesweep", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": hbm_src}
+                "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
+                "traffic_source": "ncu on the 8192-point cloud, scaled by edges",
+                "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src}
     launches_per_step = 2 + 1 + 8 + 1 + 2 + 2 + 8 + 1  # init, dist, passes, dedupe, reduce, kill sort, emit
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -255,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"every {SAMPLE_STRIDE}th point of the cloud: N={ns}, {ms_} edges, "
                          f"{dt:.1f} s single-threaded"}
     clocks = sampler.summary()
+    serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
     line = {
         "metric": METRIC, "value": world * m / (ms * 1e-3), "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -271,11 +278,73 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "serving": serving,
         "stages_ms": stages,
         "stats": {k: int(v) for k, v in st.items()},
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def percentile(vals, q):
+    return float(np.percentile(np.asarray(vals), q)) if len(vals) else None
+
+
+def run_serving(args, dev):
+    """Mixed stream (the serving workload): N log-uniform in [64, 8192], d in
+    {2,3,8,32}, Gaussian mixtures.  One-at-a-time plain calls (points in from
+    pinned host memory, bars out, synchronized) against the serving context
+    (admission by memory budget, concurrent streams, fused small-cloud
+    batches) under Poisson arrivals at 0.9x and 2x the plain rate and with
+    every cloud queued at once.  Latency = result on the host - arrival."""
+    import torch
+
+    from paper_2203_02527_gb300 import ph0
+    from paper_2203_02527_gb300.serve import Server, run_stream
+
+    clouds = inputs.stream_clouds(args.serve_clouds)
+    # plain, one at a time
+    ws = ph0.Workspace(8192, 32, dev)
+    for x in clouds[:20]:
+        ph0.barcodes(torch.from_numpy(x).to(dev), ws)
+    torch.cuda.synchronize()
+    lat, plain_bars = [], {}
+    t0 = time.perf_counter()
+    for i, x in enumerate(clouds):
+        a = time.perf_counter()
+        pts = torch.from_numpy(x).pin_memory().to(dev, non_blocking=True)
+        b = ph0.barcodes(pts, ws).raw.to("cpu")
+        lat.append(time.perf_counter() - a)
+        if i % 97 == 0:
+            plain_bars[i] = b.numpy().tobytes()
+    plain_s = time.perf_counter() - t0
+    plain_rate = len(clouds) / plain_s
+    out = {"clouds": len(clouds),
+           "plain": {"clouds_per_s": plain_rate, "p50_ms": 1e3 * percentile(lat, 50),
+                     "p99_ms": 1e3 * percentile(lat, 99)}}
+    edges = sum(len(x) * (len(x) - 1) // 2 for x in clouds)
+    out["edges"] = edges
+    checked = 0
+    with Server(mem_budget=args.serve_budget << 30, host_budget=2 << 30, streams=args.serve_streams,
+                small_max_n=180, batch_max=512) as srv:
+        run_stream(srv, clouds[:50], tag0=10_000_000)  # warm-up
+        for name, load in (("load_0.9x", 0.9), ("load_2x", 2.0), ("saturated", None)):
+            arr = None if load is None else inputs.poisson_arrivals(len(clouds), load * plain_rate)
+            t0 = time.perf_counter()
+            done = run_stream(srv, clouds, arr)
+            wall = time.perf_counter() - t0
+            first = min(f.submit_time for f in done.values())
+            last = max(f.done_time for f in done.values())
+            lats = [f.latency for f in done.values()]
+            bad = sum(f.status != 0 for f in done.values())
+            out[name] = {"clouds_per_s": len(clouds) / (last - first), "p50_ms": 1e3 * percentile(lats, 50),
+                         "p99_ms": 1e3 * percentile(lats, 99), "wall_s": wall, "errors": bad}
+            for i, want in plain_bars.items():
+                if done[i].bars.tobytes() != want:
+                    raise RuntimeError(f"served cloud {i} differs from the plain call")
+                checked += 1
+    out["bit_identical_to_plain_checked"] = checked
+    return out
 
 
 def main():
@@ -285,6 +354,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-clouds", type=int, default=10000,
+                    help="clouds in the serving stream (0 = skip the serving measurement)")
+    ap.add_argument("--serve-budget", type=int, default=64, help="serving device arena, GiB")
+    ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--n", type=int, default=32768,
                     help="points (multiple of 4); the benchmark workload is 32768")
     args = ap.parse_args()
