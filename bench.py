@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2203_02527_gb300 import inputs  # noqa: E402
+from paper_2203_02527_gb300.replicas import job_throughput, max_over_ranks, replica_seed  # noqa: E402
 
 WORKLOAD = "circles32768"
 # DRAM bytes per edge of one low radix pass (dram__bytes_read.sum +
@@ -167,7 +168,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     # each rank computes its own cloud (independent replicas)
-    x = workload_points(args, seed=inputs.DEFAULT_SEED + rank)
+    x = workload_points(args, seed=replica_seed(inputs.DEFAULT_SEED, rank))
     n, d = x.shape
     m = n * (n - 1) // 2
     pts = torch.from_numpy(x).to(dev)
@@ -199,11 +200,7 @@ def run_ours(args, rank, world, local_rank):
     st = ph0.finish(ws)
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']}")
-    ms = float(np.mean([p["total_ms"] for p in profs]))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean([p["total_ms"] for p in profs])), dev)
 
     # end to end through the public API: pinned host points in, bars out to host
     host_pts = torch.from_numpy(x).pin_memory()
@@ -221,11 +218,7 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), dev)
 
     if rank != 0:
         return
@@ -263,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.summary()
     serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
     line = {
-        "metric": METRIC, "value": world * m / (ms * 1e-3), "unit": "edges/s",
+        "metric": METRIC, "value": job_throughput(m, world, ms), "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -273,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
-        "e2e": {"value": world * m / (e2e * 1e-3), "unit": "edges/s",
+        "e2e": {"value": job_throughput(m, world, e2e), "unit": "edges/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(host_bars.numel())},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
