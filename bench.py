@@ -172,6 +172,10 @@ def run_ours(args, rank, world, local_rank):
     n, d = x.shape
     m = n * (n - 1) // 2
     pts = torch.from_numpy(x).to(dev)
+    tuning = None
+    if not args.no_tune:
+        from paper_2203_02527_gb300 import autotune
+        tuning = autotune.tune(d, n=min(n, 8192))  # cached for ph0.barcodes below
     ws = ph0.Workspace(n, d, dev)
     bars = torch.empty((n - 1, 40), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
@@ -271,6 +275,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "tuning": tuning,
         "serving": serving,
         "stages_ms": stages,
         "stats": {k: int(v) for k, v in st.items()},
@@ -347,6 +352,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
     ap.add_argument("--serve-clouds", type=int, default=10000,
                     help="clouds in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-budget", type=int, default=64, help="serving device arena, GiB")

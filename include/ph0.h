@@ -103,6 +103,25 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d);
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                  ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* Tuning of the kernels (chosen per dimension by the autotuner in the Python
+ * package; a NULL pointer or a field set to -1 selects the built-in choice).
+ * None changes any result bit. */
+typedef struct {
+    int32_t dist_split16;   /* of every 16 rows of a distance tile, how many compute the
+                               running sum on the binary64 units (the rest all in integers);
+                               0..16, built-in 16                                        */
+    int32_t dist_tile;      /* points per side of a distance tile: 32, 64 or 128; built-in
+                               128 (smaller when the tile would not fit shared memory)    */
+    int32_t sort_top_bits;  /* width of the single top radix pass: 8 or 9 (a wider top
+                               part takes two passes of 8); built-in 9                   */
+    int32_t reserved[5];
+} ph0_tuning;
+
+/* ph0_barcodes() with explicit tuning (NULL = built-in). */
+int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                       ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
+                       const ph0_tuning *tuning);
+
 /* Device time of each stage of one ph0_barcodes_profiled() call, from CUDA
  * events recorded on the caller's stream between the stages (milliseconds). */
 typedef struct {
@@ -119,7 +138,7 @@ typedef struct {
  * fills `prof` (tracing aid: same kernels, same results). */
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                           ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
-                          ph0_profile *prof);
+                          const ph0_tuning *tuning, ph0_profile *prof);
 
 /* Waits for `stream`, then returns the device status of the last call made
  * with `ws` and, when stats != NULL, its counters. */

@@ -49,6 +49,21 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("dist_split16", ctypes.c_int32), ("dist_tile", ctypes.c_int32),
+                ("sort_top_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+    @classmethod
+    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1):
+        t = cls()
+        t.dist_split16, t.dist_tile, t.sort_top_bits = dist_split16, dist_tile, sort_top_bits
+        return t
+
+    def as_dict(self):
+        return {"dist_split16": self.dist_split16, "dist_tile": self.dist_tile,
+                "sort_top_bits": self.sort_top_bits}
+
+
 class Profile(ctypes.Structure):
     _fields_ = [
         ("total_ms", ctypes.c_float), ("dist_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
@@ -91,8 +106,10 @@ SIGNATURES = {
     "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
     "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
+    "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
+                                          ctypes.POINTER(Tuning)]),
     "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
-                                             ctypes.POINTER(Profile)]),
+                                             ctypes.POINTER(Tuning), ctypes.POINTER(Profile)]),
     "ph0_trace_windows": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32]),
     "ph0_barcodes_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP]),
     "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),

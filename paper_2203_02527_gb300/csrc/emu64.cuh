@@ -54,15 +54,14 @@ __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 }
 
 // Round a significand with bit 63 set (bit 0 may hold a sticky bit) to 53
-// bits, nearest-even.  Branch-free.
+// bits, nearest-even, in place (the round and sticky bits are in the low
+// word).  Branch-free.
 __host__ __device__ __forceinline__ F53 round53(uint64_t m, int32_t e) {
-    uint64_t keep = m >> 11;
-    const uint64_t half = (m >> 10) & 1u;
-    const uint64_t sticky = (m & 0x3ffu) != 0;
-    keep += half & (sticky | (keep & 1u));
-    const uint32_t over = uint32_t(keep >> 53);  // rounded up to 2^53
-    keep >>= over;
-    return F53{keep << 11, e + int32_t(over)};
+    const uint32_t lo = uint32_t(m);
+    const uint32_t up = (lo >> 10) & (((lo & 0x3ffu) != 0) | (lo >> 11)) & 1u;
+    const uint64_t t = m + (uint64_t(up) << 11);
+    const bool over = t < m;  // carried out of bit 63: the value is 2^64
+    return F53{over ? (uint64_t(1) << 63) : (t & ~uint64_t(0x7ff)), e + int32_t(over)};
 }
 
 // RN(t*t) for t = a * 2^g, 0 <= a < 2^53.  Branch-free; a = 0 gives zero.
@@ -76,6 +75,15 @@ __host__ __device__ __forceinline__ F53 square53(uint64_t a, int32_t g) {
     const uint64_t m = top ? (hi | uint64_t(lo != 0))
                            : ((hi << 1) | (lo >> 63) | uint64_t((lo << 1) != 0));
     F53 r = round53(m, 2 * ea + int32_t(top));
+    if (a == 0) r = F53{0, kZeroExp};
+    return r;
+}
+
+// RN(t*t) for t = a * 2^g with a < 2^32 (a 32x32 -> 64-bit product, exact).
+__host__ __device__ __forceinline__ F53 square53_narrow(uint32_t a, int32_t g) {
+    const uint64_t p = uint64_t(a) * a;
+    const int lz = clz64(p | 1u);
+    F53 r = round53(p << lz, 63 - lz + 2 * g);
     if (a == 0) r = F53{0, kZeroExp};
     return r;
 }
@@ -142,15 +150,62 @@ __host__ __device__ __forceinline__ int64_t to_fixed(uint32_t bits, int32_t g) {
 }
 
 // Squared distance from fixed-point coordinates of one edge (X[k] in units of
-// 2^g[k]); every |X| < 2^52.
+// 2^g[k]); every |X| < 2^52.  Dimensions whose bit `k` is set in `narrow`
+// (coordinates below 2^31 in magnitude) use the 32-bit square.
 __host__ __device__ __forceinline__ uint64_t sq_dist_fixed(const int64_t *xu, const int64_t *xv,
-                                                           const int32_t *g, int d, int su, int sv) {
+                                                           const int32_t *g, int d, int su, int sv,
+                                                           const uint32_t *narrow = nullptr) {
     F53 s{0, kZeroExp};
     for (int k = 0; k < d; ++k) {
         const int64_t t = xv[k * sv] - xu[k * su];
-        s = add53(s, square53(uint64_t(t < 0 ? -t : t), g[k]));
+        const uint64_t a = uint64_t(t < 0 ? -t : t);
+        F53 p;
+        if (narrow && ((narrow[k >> 5] >> (k & 31)) & 1u)) p = square53_narrow(uint32_t(a), g[k]);
+        else p = square53(a, g[k]);
+        s = add53(s, p);
     }
     return to_bits(s);
+}
+
+// binary64 value of an F53 (normal range).
+__host__ __device__ __forceinline__ double to_double(F53 s) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)to_bits(s));
+#else
+    const uint64_t b = to_bits(s);
+    double x;
+    __builtin_memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
+// The same squared distance with the squares RN(t*t) formed exactly with
+// integers and the running sum s = RN(s + p) taken by the binary64 adder
+// (16 binary64 operations per edge at d = 16 instead of 47).
+__host__ __device__ __forceinline__ uint64_t sq_dist_mixed(const int64_t *xu, const int64_t *xv,
+                                                           const int32_t *g, int d, int su, int sv,
+                                                           const uint32_t *narrow = nullptr) {
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const int64_t t = xv[k * sv] - xu[k * su];
+        const uint64_t a = uint64_t(t < 0 ? -t : t);
+        F53 p;
+        if (narrow && ((narrow[k >> 5] >> (k & 31)) & 1u)) p = square53_narrow(uint32_t(a), g[k]);
+        else p = square53(a, g[k]);
+#ifdef __CUDA_ARCH__
+        s = __dadd_rn(s, to_double(p));
+#else
+        volatile double sum = s + to_double(p);
+        s = sum;
+#endif
+    }
+#ifdef __CUDA_ARCH__
+    return uint64_t(__double_as_longlong(s));
+#else
+    uint64_t b;
+    __builtin_memcpy(&b, &s, 8);
+    return b;
+#endif
 }
 
 }  // namespace emu

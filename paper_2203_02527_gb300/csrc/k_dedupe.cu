@@ -27,7 +27,7 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
     __shared__ int64_t s_excl;
 
     const uint64_t *keys = keys0;
-    if (sort_h) keys = (make_plan(sort_h->kmin, sort_h->kmax).passes & 1) ? keys1 : keys0;
+    if (sort_h) keys = (make_plan(sort_h).passes & 1) ? keys1 : keys0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(&h->tile_counter[kMaxPasses], 1u);
     __syncthreads();

@@ -26,11 +26,13 @@
 namespace ph0 {
 
 constexpr int kDistThreads = 256;
-// On integer-path tiles, rows i with (i % 16) < kDistHwRows16 still use the
-// binary64 units: the two pipes run concurrently, and an even split measured
-// fastest on GB300 (30 ms vs 46 ms integer-only and 50 ms binary64-only for
-// 537M edges at d = 16).  Both paths give identical bits.
-constexpr int kDistHwRows16 = 8;
+// On integer-path tiles, rows i with (i % 16) < split16 form the squares with
+// integers and take the running sums on the binary64 units (16 binary64
+// operations per edge at d = 16 instead of 47); the other rows are computed
+// all in integers.  The two pipes run concurrently; all rows on the mixed
+// form measured fastest on GB300 for d = 16 (24 ms vs 42 ms all-integer and
+// 50 ms binary64-only for 537M edges), and the autotuner picks the split per
+// dimension.  All forms give identical bits.
 
 // Squared distance of one edge: s = 0; t = x_v - x_u; s = s + t*t per
 // dimension, each operation rounded to nearest (no contraction).
@@ -77,11 +79,10 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     double *sv = s_coord + size_t(d) * bt;
     int64_t *xu = reinterpret_cast<int64_t *>(su);
     int64_t *xv = reinterpret_cast<int64_t *>(sv);
-    double *fu = s_coord + size_t(2) * d * bt;      // binary64 copies for the split rows
-    double *fv = fu + size_t(d) * bt;
-    int32_t *s_g = reinterpret_cast<int32_t *>(s_coord + size_t(4) * d * bt);
+    int32_t *s_g = reinterpret_cast<int32_t *>(s_coord + size_t(2) * d * bt);
     int32_t *s_lo = s_g + d;
     int32_t *s_hi = s_lo + d;
+    uint32_t *s_narrow = reinterpret_cast<uint32_t *>(s_hi + d);  // [(d+31)/32]
 
     for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) (&s_hist[0][0])[b] = 0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
@@ -110,10 +111,13 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     __syncthreads();
     if (threadIdx.x == 0) {
         int fixed = 1;
+        for (int w = 0; w < (d + 31) / 32; ++w) s_narrow[w] = 0;
         for (int k = 0; k < d; ++k) {
             const bool zero = s_lo[k] == (1 << 30);
             s_g[k] = zero ? 0 : s_lo[k];
-            if (!zero && s_hi[k] + 1 - s_lo[k] > 52) fixed = 0;
+            const int span = zero ? 0 : s_hi[k] + 1 - s_lo[k];
+            if (span > 52) fixed = 0;
+            if (span <= 31) s_narrow[k >> 5] |= 1u << (k & 31);  // |X| < 2^31: 32-bit squares
         }
         s_fixed = fixed;
         atomicAdd(&h->dist_tiles, 1ull);
@@ -129,8 +133,6 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         if (fixed) {
             xu[k * bt + p] = emu::to_fixed(__float_as_uint(a), s_g[k]);
             xv[k * bt + p] = emu::to_fixed(__float_as_uint(b), s_g[k]);
-            fu[k * bt + p] = double(a);
-            fv[k * bt + p] = double(b);
         } else {
             su[k * bt + p] = double(a);
             sv[k * bt + p] = double(b);
@@ -147,8 +149,8 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         if (u < v && v < n) {
             uint64_t kb;
             if (!fixed) kb = uint64_t(__double_as_longlong(sq_dist_f64(su, sv, d, bt, i, j)));
-            else if ((i & 15) < hw16) kb = uint64_t(__double_as_longlong(sq_dist_f64(fu, fv, d, bt, i, j)));
-            else kb = emu::sq_dist_fixed(xu + i, xv + j, s_g, d, bt, bt);
+            else if ((i & 15) < hw16) kb = emu::sq_dist_mixed(xu + i, xv + j, s_g, d, bt, bt, s_narrow);
+            else kb = emu::sq_dist_fixed(xu + i, xv + j, s_g, d, bt, bt, s_narrow);
             int64_t e = edge_index(n, u, v);
             key[e] = kb;
             val[e] = (uint32_t(u) << 16) | uint32_t(v);
@@ -188,20 +190,21 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
 
 // Shared memory of a tile: two staged blocks plus g, lo, hi per dimension.
 size_t dist_smem(int bt, int d) {
-    return size_t(4) * bt * d * sizeof(double) + size_t(3) * d * sizeof(int32_t);
+    return size_t(2) * bt * d * sizeof(double) + size_t(3) * d * sizeof(int32_t) +
+           size_t((d + 31) / 32) * sizeof(uint32_t);
 }
 
 // Tile edge for dimension d: the staged blocks must fit in shared memory.
-int dist_tile(int d) {
-    int bt = 128;
+int dist_tile(int d, int want) {
+    int bt = (want == 32 || want == 64) ? want : 128;
     while (bt > 8 && dist_smem(bt, d) > 160 * 1024) bt /= 2;
     return bt;
 }
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
-                        uint32_t *val, Header *h, cudaStream_t s) {
+                        uint32_t *val, Header *h, cudaStream_t s, int split16, int tile) {
     if (n < 2) return cudaSuccess;
-    const int bt = dist_tile(d);
+    const int bt = dist_tile(d, tile);
     const size_t smem = dist_smem(bt, d);
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_dist, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -209,7 +212,8 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
     if (e != cudaSuccess) return e;
     const int64_t T = (n + bt - 1) / bt;
     const int64_t tiles = T * (T + 1) / 2;
-    k_dist<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, kDistHwRows16, key,
+    const int hw16 = (split16 >= 0 && split16 <= 16) ? split16 : kDefaultDistSplit16;
+    k_dist<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, hw16, key,
                                                        val, h);
     return cudaGetLastError();
 }

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     const int64_t n = A.n, m = A.m;
     if (m <= 0) return;
     const uint32_t *val = A.val0;
-    if (A.sort_h) val = (make_plan(A.sort_h->kmin, A.sort_h->kmax).passes & 1) ? A.val1 : A.val0;
+    if (A.sort_h) val = (make_plan(A.sort_h).passes & 1) ? A.val1 : A.val0;
     const int tid = threadIdx.x;
     const int64_t G = gridDim.x;
     const int64_t gtid = int64_t(blockIdx.x) * kReduceThreads + tid;
@@ -465,8 +465,8 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
                        ph0_bar *bars) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= nb) return;
-    const bool kodd = kill_h && (make_plan(kill_h->kmin, kill_h->kmax).passes & 1);
-    const bool sodd = sort_h && (make_plan(sort_h->kmin, sort_h->kmax).passes & 1);
+    const bool kodd = kill_h && (make_plan(kill_h).passes & 1);
+    const bool sodd = sort_h && (make_plan(sort_h).passes & 1);
     const unsigned long long p = kodd ? kk1[j] : kk0[j];
     const uint32_t low = kodd ? kv1[j] : kv0[j];
     if (p >= (unsigned long long)m) {  // fewer pivots than n-1: only after a reported error

@@ -4,8 +4,9 @@
 // A persistent kernel takes clouds from a task table (atomic counter); one
 // CTA computes a cloud entirely in shared memory:
 //   1. all E = n(n-1)/2 squared distances (the same rounded binary64 sequence
-//      as k_dist, by the exact integer emulation when the cloud's coordinates
-//      fit 52 bits per dimension, else by the binary64 units),
+//      as k_dist: squares formed exactly with integers and sums on the
+//      binary64 units when the cloud's coordinates fit 52 bits per dimension,
+//      else all on the binary64 units),
 //   2. a bitonic sort of (distance bits, edge id) -- the same total order
 //      (distance, u, v) as the radix sort,
 //   3. de-duplication: a = inclusive count of new distances (block scan),
@@ -34,6 +35,7 @@ struct SmallSmem {
     uint32_t kpos[256];
     uint16_t klow[256];
     int32_t g[kSmallMaxD], lo[kSmallMaxD], hi[kSmallMaxD];
+    uint32_t narrow[(kSmallMaxD + 31) / 32];
     uint32_t warp_sum[kSmallThreads / 32 + 1];
     uint32_t npiv, left, task, fixed_ok, bad;
 };
@@ -86,10 +88,13 @@ __device__ void small_cloud(const SmallTask &T, SmallSmem &S) {
     __syncthreads();
     if (tid == 0) {
         uint32_t ok = 1;
+        for (int w = 0; w < (kSmallMaxD + 31) / 32; ++w) S.narrow[w] = 0;
         for (int k = 0; k < d; ++k) {
             const bool zero = S.lo[k] == (1 << 30);
             S.g[k] = zero ? 0 : S.lo[k];
-            if (!zero && S.hi[k] + 1 - S.lo[k] > 52) ok = 0;
+            const int span = zero ? 0 : S.hi[k] + 1 - S.lo[k];
+            if (span > 52) ok = 0;
+            if (span <= 31) S.narrow[k >> 5] |= 1u << (k & 31);
         }
         S.fixed_ok = ok;
     }
@@ -109,7 +114,7 @@ __device__ void small_cloud(const SmallTask &T, SmallSmem &S) {
             int u, v;
             edge_of(e, n, u, v);
             if (fixed) {
-                kb = emu::sq_dist_fixed(T.fixed + u, T.fixed + v, S.g, d, n, n);
+                kb = emu::sq_dist_mixed(T.fixed + u, T.fixed + v, S.g, d, n, n, S.narrow);
             } else {
                 double s = 0.0;
                 for (int k = 0; k < d; ++k) {

@@ -53,7 +53,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp
 }
 
 // Header fields a sort needs zeroed: histograms, key range, tile counters.
-__global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words) {
+__global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int top_bits) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     if (tid == 0) {
@@ -61,6 +61,7 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words) {
         h->kmax = 0;
         h->sort_passes = 0;
         h->key_bits = 0;
+        h->top_bits = top_bits;
     }
     for (int64_t i = tid; i < int64_t(kMaxPasses) * kMaxRadix; i += stride)
         (&h->hist[0][0])[i] = 0;
@@ -237,7 +238,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     extern __shared__ __align__(16) unsigned char s_raw[];
     SortSmem<RADIX> &S = *reinterpret_cast<SortSmem<RADIX> *>(s_raw);
 
-    const Plan plan = make_plan(h->kmin, h->kmax);
+    const Plan plan = make_plan(h);
     if (SLOT >= plan.passes) return;
     const uint64_t *kin = (SLOT & 1) ? keys1 : keys0;
     uint64_t *kout = (SLOT & 1) ? keys0 : keys1;
@@ -405,7 +406,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 // copy it into buffer 0 (used when the caller's buffer must hold the result).
 __global__ void k_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                               const uint32_t *vals1, int64_t m, const Header *h) {
-    const Plan plan = make_plan(h->kmin, h->kmax);
+    const Plan plan = make_plan(h);
     if ((plan.passes & 1) == 0) return;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += int64_t(gridDim.x) * blockDim.x) {
@@ -426,12 +427,12 @@ int sm_count() {
 }
 
 // Zero the sort's counters and first look-back buffer (sized for 512 buckets).
-cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s) {
+cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s, int top_bits) {
     const int64_t words = tiles * kMaxRadix;
     int blocks = int((words + 255) / 256);
     if (blocks < 8) blocks = 8;
     if (blocks > 4 * sm_count() * 8) blocks = 4 * sm_count() * 8;
-    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words);
+    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words, top_bits == 8 ? 8 : 9);
     return cudaGetLastError();
 }
 

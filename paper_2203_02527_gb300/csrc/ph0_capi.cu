@@ -11,8 +11,9 @@
 namespace ph0 {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
-                        uint32_t *val, Header *h, cudaStream_t s);
-cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s);
+                        uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1);
+cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
+                             int top_bits = kDefaultTopBits);
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
@@ -54,12 +55,23 @@ int64_t n_for_edges(int64_t m) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PH0_OK : PH0_ECUDA; }
 
+// Tuning with the built-in choices filled in.
+struct Tune {
+    int split16 = kDefaultDistSplit16, tile = -1, top_bits = kDefaultTopBits;
+    explicit Tune(const ph0_tuning *t) {
+        if (!t) return;
+        if (t->dist_split16 >= 0 && t->dist_split16 <= 16) split16 = t->dist_split16;
+        if (t->dist_tile == 32 || t->dist_tile == 64 || t->dist_tile == 128) tile = t->dist_tile;
+        if (t->sort_top_bits == 8 || t->sort_top_bits == 9) top_bits = t->sort_top_bits;
+    }
+};
+
 // Zero the header and prepare the main sort (first look-back buffer).
-cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s) {
+cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s, int top_bits = kDefaultTopBits) {
     Header *h = at<Header>(ws, L.hdr);
     cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
     if (e != cudaSuccess) return e;
-    return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s);
+    return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s, top_bits);
 }
 
 // Steps 4-5 plus the read-out: reduce, order the pivot columns by position,
@@ -146,21 +158,22 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d) {
     return Layout(n, d).total;
 }
 
-int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
-                 void *ws, size_t ws_bytes, void *stream) {
+int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                       void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
     if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
+    const Tune t(tuning);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
     uint32_t *a = at<uint32_t>(ws, L.a);
-    cudaError_t e = begin_call(ws, L, s);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
+    cudaError_t e = begin_call(ws, L, s, t.top_bits);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess)
         e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
                                at<uint64_t>(ws, L.look[1]), h, s);
@@ -169,9 +182,14 @@ int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar
     return cuda_status(e);
 }
 
+int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                 void *ws, size_t ws_bytes, void *stream) {
+    return ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, ws, ws_bytes, stream, nullptr);
+}
+
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                           ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
-                          ph0_profile *prof) {
+                          const ph0_tuning *tuning, ph0_profile *prof) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || !prof || (n > 1 && !bars_dev)) return PH0_EINVAL;
@@ -195,9 +213,10 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     }
     // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | dedupe | ev[2+P] | reduce | ev[3+P] |
     // order pivots, emit | ev[4+P]   (P = kMaxPasses launches; unneeded passes return at once)
+    const Tune t(tuning);
     e = cudaEventRecord(ev[0], s);
-    if (e == cudaSuccess) e = begin_call(ws, L, s);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
+    if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {

@@ -60,7 +60,8 @@ struct Header {
     int32_t abort;
     uint32_t npiv;               // pivots claimed so far
     uint32_t nlist[2];           // candidate list lengths (ping-pong)
-    uint32_t pad[6];
+    int32_t top_bits;            // width of a single top radix pass (8 or 9)
+    uint32_t pad[5];
     uint32_t hist[kMaxPasses][kMaxRadix];  // digit histogram per radix pass
 };
 
@@ -208,7 +209,7 @@ __host__ __device__ __forceinline__ int bitlen64(uint64_t x) {
     return x ? 64 - __builtin_clzll(x) : 0;
 #endif
 }
-__host__ __device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax) {
+__host__ __device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax, int top_bits = 9) {
     Plan p;
     p.kmin = kmin;
     if (kmax < kmin) kmax = kmin;  // no keys
@@ -220,12 +221,20 @@ __host__ __device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax)
     } else {
         const int tb = bitlen64((kmax >> kTopShift) - (kmin >> kTopShift));
         p.low = kLowPasses;
-        p.top = tb <= 9 ? 1 : 2;
+        p.top = tb <= (top_bits == 8 ? 8 : 9) ? 1 : 2;
         p.bits = kTopShift + tb;
     }
     p.passes = p.low + p.top;
     return p;
 }
+__host__ __device__ __forceinline__ Plan make_plan(const Header *h) {
+    return make_plan(h->kmin, h->kmax, h->top_bits);
+}
+
+// Built-in tuning (ph0_tuning fields of -1).
+constexpr int kDefaultDistSplit16 = 16;
+constexpr int kDefaultTopBits = 9;
+
 // Digit of a key in a pass (< 512 in a single top pass, else < 256).
 __host__ __device__ __forceinline__ uint32_t digit_of(uint64_t key, const Plan &p, int pass) {
     if (pass < p.low) return uint32_t(key >> (kRadixBits * pass)) & (kRadix - 1);

@@ -93,22 +93,35 @@ def _points(pts: torch.Tensor):
     return pts, pts.shape[0], pts.shape[1], pts.stride(0)
 
 
+def _tuning(d: int, tuning):
+    """Explicit tuning, else the autotuner's cached choice for this dimension
+    (None: the library's built-in choice)."""
+    if tuning is not None:
+        return tuning if isinstance(tuning, _lib.Tuning) else _lib.Tuning.make(**tuning)
+    from . import autotune
+    t = autotune.cached(d)
+    return _lib.Tuning.make(**t) if t else None
+
+
 def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False,
-             sync: bool = True) -> Bars:
+             sync: bool = True, tuning=None) -> Bars:
     """Finite bars of the 0th persistent homology of the point cloud (steps 1-5)."""
     pts, n, d, ld = _points(pts)
     ws = ws or _workspace(n, d, pts.device)
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     s = _stream()
     lib = _lib.load()
-    check(lib.ph0_barcodes(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, s), "ph0_barcodes")
+    t = _tuning(d, tuning)
+    check(lib.ph0_barcodes_tuned(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, s,
+                                 ctypes.byref(t) if t is not None else None), "ph0_barcodes")
     st = None
     if sync or stats:
         st = finish(ws)
     return Bars(bars, n, st)
 
 
-def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None):
+def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None,
+                      tuning=None):
     """ph0_barcodes with CUDA events between the stages (waits for the stream).
     Returns (Bars, per-stage milliseconds)."""
     pts, n, d, ld = _points(pts)
@@ -116,8 +129,10 @@ def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torc
     if bars is None:
         bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     prof = _lib.Profile()
+    t = _tuning(d, tuning)
     check(_lib.load().ph0_barcodes_profiled(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes,
-                                            _stream(), ctypes.byref(prof)), "ph0_barcodes_profiled")
+                                            _stream(), ctypes.byref(t) if t is not None else None,
+                                            ctypes.byref(prof)), "ph0_barcodes_profiled")
     return Bars(bars, n, None), prof.as_dict()
 
 

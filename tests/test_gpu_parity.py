@@ -169,3 +169,26 @@ def test_step_oracle_pins_hold_on_gpu_output():
     assert pins.check_bars_structure(60, got, 0) is None
     assert pins.check_bars_kruskal(x, got) is None
     assert pins.check_bars_sweep(x[:12], ph0.barcodes(_cuda(x[:12])).numpy()) is None
+
+
+@pytest.mark.parametrize("split,tile,top", [(0, 128, 9), (5, 64, 9), (16, 32, 8), (11, 128, 8)])
+def test_tuning_changes_no_bit(split, tile, top):
+    """Every tuning (distance split, tile size, top radix width) gives the
+    oracle's bars; clouds with zero distances make the key range span more
+    than 9 top bits (two top passes)."""
+    ph0 = _ph0()
+    t = {"dist_split16": split, "dist_tile": tile, "sort_top_bits": top}
+    for x in (inputs.noisy_circles(150, 4, 8, seed=91), inputs.with_duplicates(500, 3, 300, seed=92),
+              inputs.exponent_gaps(200, 4, seed=93)):
+        got = ph0.barcodes(_cuda(x), tuning=t).numpy()
+        assert_bars_equal(got, oracle.barcodes(x)[0])
+
+
+def test_autotuner_picks_valid_settings(tmp_path, monkeypatch):
+    monkeypatch.setenv("PH0_TUNING_CACHE", str(tmp_path / "tuning.json"))
+    from paper_2203_02527_gb300 import autotune
+    monkeypatch.setattr(autotune, "_cache", None)
+    t = autotune.tune(3, n=1024, repeats=1)
+    assert t["dist_split16"] in (0, 4, 8, 12, 16)
+    assert t["dist_tile"] in (64, 128) and t["sort_top_bits"] in (8, 9)
+    assert autotune.cached(3) == t
