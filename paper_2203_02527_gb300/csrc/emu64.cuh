@@ -179,25 +179,59 @@ __host__ __device__ __forceinline__ double to_double(F53 s) {
 #endif
 }
 
+// binary64 bit pattern of RN(t*t) for t = a * 2^g with 0 <= a < 2^31: the
+// exact square has at most 62 bits; after normalizing it to bit 63, adding
+// the rounding increment to the 53-bit significand lets a carry flow into the
+// exponent field (bits = (exponent - 1) << 52 plus the significand with its
+// leading bit), so no overflow case is needed.
+__host__ __device__ __forceinline__ uint64_t square_bits_narrow(uint32_t a, int32_t g) {
+    const uint64_t p = uint64_t(a) * a;
+    const int lz = clz64(p | 1u);
+    const uint64_t pn = p << lz;
+    const uint32_t lo = uint32_t(pn);
+    const uint32_t up = (lo >> 10) & (((lo & 0x3ffu) != 0) | (lo >> 11)) & 1u;
+    const uint64_t bits = (uint64_t(int64_t(63 - lz + 2 * g + 1023 - 1)) << 52) + ((pn >> 11) + up);
+    return a ? bits : 0;
+}
+
+__host__ __device__ __forceinline__ double bits_to_double(uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    __builtin_memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
 // The same squared distance with the squares RN(t*t) formed exactly with
 // integers and the running sum s = RN(s + p) taken by the binary64 adder
 // (16 binary64 operations per edge at d = 16 instead of 47).
 __host__ __device__ __forceinline__ uint64_t sq_dist_mixed(const int64_t *xu, const int64_t *xv,
                                                            const int32_t *g, int d, int su, int sv,
                                                            const uint32_t *narrow = nullptr) {
+    // `narrow` bit k: every |X| of dimension k is below 2^30, so t fits a
+    // 32-bit signed difference of the low words
     double s = 0.0;
     for (int k = 0; k < d; ++k) {
-        const int64_t t = xv[k * sv] - xu[k * su];
-        const uint64_t a = uint64_t(t < 0 ? -t : t);
-        F53 p;
-        if (narrow && ((narrow[k >> 5] >> (k & 31)) & 1u)) p = square53_narrow(uint32_t(a), g[k]);
-        else p = square53(a, g[k]);
+        double p;
+        if (narrow && ((narrow[k >> 5] >> (k & 31)) & 1u)) {
+            const int32_t t = int32_t(uint32_t(xv[k * sv])) - int32_t(uint32_t(xu[k * su]));
+            p = bits_to_double(square_bits_narrow(uint32_t(t < 0 ? -t : t), g[k]));
+        } else {
+            const int64_t t = xv[k * sv] - xu[k * su];
+            p = to_double(square53(uint64_t(t < 0 ? -t : t), g[k]));
+        }
+        if (k == 0) {
+            s = p;  // 0 + p is exact
+        } else {
 #ifdef __CUDA_ARCH__
-        s = __dadd_rn(s, to_double(p));
+            s = __dadd_rn(s, p);
 #else
-        volatile double sum = s + to_double(p);
-        s = sum;
+            volatile double sum = s + p;
+            s = sum;
 #endif
+        }
     }
 #ifdef __CUDA_ARCH__
     return uint64_t(__double_as_longlong(s));

@@ -82,7 +82,8 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     int32_t *s_g = reinterpret_cast<int32_t *>(s_coord + size_t(2) * d * bt);
     int32_t *s_lo = s_g + d;
     int32_t *s_hi = s_lo + d;
-    uint32_t *s_narrow = reinterpret_cast<uint32_t *>(s_hi + d);  // [(d+31)/32]
+    uint32_t *s_narrow = reinterpret_cast<uint32_t *>(s_hi + d);  // [(d+31)/32] span <= 31 bits
+    uint32_t *s_narrow30 = s_narrow + (d + 31) / 32;                // [(d+31)/32] span <= 30 bits
 
     for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) (&s_hist[0][0])[b] = 0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
@@ -111,13 +112,14 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     __syncthreads();
     if (threadIdx.x == 0) {
         int fixed = 1;
-        for (int w = 0; w < (d + 31) / 32; ++w) s_narrow[w] = 0;
+        for (int w = 0; w < (d + 31) / 32; ++w) s_narrow[w] = s_narrow30[w] = 0;
         for (int k = 0; k < d; ++k) {
             const bool zero = s_lo[k] == (1 << 30);
             s_g[k] = zero ? 0 : s_lo[k];
             const int span = zero ? 0 : s_hi[k] + 1 - s_lo[k];
             if (span > 52) fixed = 0;
-            if (span <= 31) s_narrow[k >> 5] |= 1u << (k & 31);  // |X| < 2^31: 32-bit squares
+            if (span <= 31) s_narrow[k >> 5] |= 1u << (k & 31);    // |X| < 2^31: 32-bit squares
+            if (span <= 30) s_narrow30[k >> 5] |= 1u << (k & 31);  // |X| < 2^30: 32-bit differences
         }
         s_fixed = fixed;
         atomicAdd(&h->dist_tiles, 1ull);
@@ -149,7 +151,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         if (u < v && v < n) {
             uint64_t kb;
             if (!fixed) kb = uint64_t(__double_as_longlong(sq_dist_f64(su, sv, d, bt, i, j)));
-            else if ((i & 15) < hw16) kb = emu::sq_dist_mixed(xu + i, xv + j, s_g, d, bt, bt, s_narrow);
+            else if ((i & 15) < hw16) kb = emu::sq_dist_mixed(xu + i, xv + j, s_g, d, bt, bt, s_narrow30);
             else kb = emu::sq_dist_fixed(xu + i, xv + j, s_g, d, bt, bt, s_narrow);
             int64_t e = edge_index(n, u, v);
             key[e] = kb;
@@ -191,7 +193,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
 // Shared memory of a tile: two staged blocks plus g, lo, hi per dimension.
 size_t dist_smem(int bt, int d) {
     return size_t(2) * bt * d * sizeof(double) + size_t(3) * d * sizeof(int32_t) +
-           size_t((d + 31) / 32) * sizeof(uint32_t);
+           size_t(2) * ((d + 31) / 32) * sizeof(uint32_t);
 }
 
 // Tile edge for dimension d: the staged blocks must fit in shared memory.

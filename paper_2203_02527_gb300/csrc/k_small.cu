@@ -94,7 +94,7 @@ __device__ void small_cloud(const SmallTask &T, SmallSmem &S) {
             S.g[k] = zero ? 0 : S.lo[k];
             const int span = zero ? 0 : S.hi[k] + 1 - S.lo[k];
             if (span > 52) ok = 0;
-            if (span <= 31) S.narrow[k >> 5] |= 1u << (k & 31);
+            if (span <= 30) S.narrow[k >> 5] |= 1u << (k & 31);  // 32-bit differences
         }
         S.fixed_ok = ok;
     }

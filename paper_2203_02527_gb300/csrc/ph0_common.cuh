@@ -28,7 +28,10 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 
 // Radix sort tile: kSortThreads threads x kSortItems keys.
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+#ifndef PH0_SORT_ITEMS
+#define PH0_SORT_ITEMS 16
+#endif
+constexpr int kSortItems = PH0_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 // Look-back status word: [63:62] flag, [61:0] count.

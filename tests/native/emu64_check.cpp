@@ -57,7 +57,7 @@ int main(int argc, char **argv) {
         }
         // per-dimension scale g_k and the 52-bit bound, as the kernel does
         std::vector<int32_t> g(d);
-        std::vector<uint32_t> narrow((d + 31) / 32, 0u);
+        std::vector<uint32_t> narrow((d + 31) / 32, 0u), narrow30((d + 31) / 32, 0u);
         bool ok = true;
         for (int k = 0; k < d; ++k) {
             int32_t lo = 1 << 30, hi = -(1 << 30);
@@ -72,7 +72,8 @@ int main(int argc, char **argv) {
             if (lo == (1 << 30)) { g[k] = 0; continue; }
             g[k] = lo;
             if (hi + 1 - lo > 52) ok = false;
-            if (hi + 1 - lo <= 31) narrow[k >> 5] |= 1u << (k & 31);  // |X| < 2^31: 32-bit squares
+            if (hi + 1 - lo <= 31) narrow[k >> 5] |= 1u << (k & 31);    // |X| < 2^31: 32-bit squares
+            if (hi + 1 - lo <= 30) narrow30[k >> 5] |= 1u << (k & 31);  // |X| < 2^30: 32-bit differences
         }
         if (!ok) { ++skipped; continue; }
         std::vector<int64_t> X(size_t(P) * d);
@@ -84,7 +85,7 @@ int main(int argc, char **argv) {
                 const uint64_t got_n =
                     sq_dist_fixed(&X[size_t(i) * d], &X[size_t(j) * d], g.data(), d, 1, 1, narrow.data());
                 const uint64_t got_m =
-                    sq_dist_mixed(&X[size_t(i) * d], &X[size_t(j) * d], g.data(), d, 1, 1, narrow.data());
+                    sq_dist_mixed(&X[size_t(i) * d], &X[size_t(j) * d], g.data(), d, 1, 1, narrow30.data());
                 const double want = ref_d2(&x[size_t(i) * d], &x[size_t(j) * d], d);
                 uint64_t wb;
                 std::memcpy(&wb, &want, 8);
