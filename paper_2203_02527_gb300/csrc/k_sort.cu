@@ -3,21 +3,24 @@
 // used a library sort, Sec. 4.1).
 //
 // A stable least-significant-digit radix sort of (key = binary64 bit pattern
-// of the squared distance, val = (u << 16) | v) pairs, one 8-bit digit per
-// pass.  The keys are non-negative doubles, so their unsigned bit patterns
-// are in numeric order; the edges enter in val order, so stability gives the
-// total order (distance, u, v).  Only the bits in which the keys differ are
-// sorted (see make_plan).
+// of the squared distance, val = (u << 16) | v) pairs.  The keys are
+// non-negative doubles, so their unsigned bit patterns are in numeric order;
+// the edges enter in val order, so stability gives the total order
+// (distance, u, v).  The low 48 bits are six 8-bit digits; above them only
+// the bits in which the keys differ are sorted, as one 9-bit digit or two
+// 8-bit digits (see make_plan).
 //
 // Each pass is a single kernel ("one sweep"): a CTA takes the next tile of
 // kSortTile keys (tile ids from an atomic counter, so every tile it waits on
 // belongs to a CTA already running), ranks the keys of its tile stably by
-// digit with warp match, publishes its per-digit counts, and obtains the
-// counts of all earlier tiles by decoupled look-back over per-tile status
-// words.  The tile is reordered by digit in shared memory and written out as
-// contiguous runs, one run per digit.  While writing, it histograms the next
-// pass's digit, so no pass needs an extra read of the keys.  Every wait is
-// bounded.
+// digit, publishes its per-digit counts, and obtains the counts of all
+// earlier tiles by decoupled look-back over per-tile status words.  Ranking
+// finds the lanes of a warp that share a digit by intersecting one warp
+// ballot per digit bit.  The tile is reordered by digit in shared memory and
+// written out as contiguous runs, one run per digit.  The six low-digit
+// histograms come from the distance kernel; the last low pass histograms the
+// top digit(s) while it writes, so no pass needs an extra read of the keys.
+// Every wait is bounded.
 #include "ph0_common.cuh"
 
 namespace ph0 {
@@ -119,16 +122,15 @@ template <int RADIX>
 struct SortSmem {
     static constexpr int W = kSortThreads / 32;
     uint64_t keys[kSortTile];          // input keys, then the tile's keys in sorted order
-    uint32_t vals_in[kSortTile];       // input values
+    uint32_t vals_in[kSortTile];       // input values; after the scatter, the top-digit histogram
     uint32_t vals[kSortTile];          // values in sorted order
-    uint16_t whist[W][RADIX];          // counts, then exclusive warp offsets
-    int64_t gofs[RADIX];               // global position of sorted tile index 0 of each digit's run
-    uint32_t lstart[RADIX];            // local start of each digit in the tile
-    uint32_t next[kMaxRadix];          // histogram(s) of the top digit(s) (last low pass only)
+    uint16_t whist[W][RADIX];          // counts, then the local position of each warp's first item
+    int32_t gofs[RADIX];               // global position of sorted tile index 0 of each digit's run
     uint32_t scan[W + 1];
     uint32_t tile;
     unsigned long long mbar;           // completion of the tile's bulk copies
 };
+static_assert(kMaxRadix <= kSortTile, "top-digit histogram lives in vals_in");
 
 // ---- bulk (TMA) copies global -> shared with an mbarrier -------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -209,12 +211,17 @@ __device__ __forceinline__ int64_t lookback_window(const uint64_t *col, int64_t 
         }
         if (done) break;
         t -= folded;
-        if (blocked) {
-            if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
-                set_status(h, PH0_ETIMEOUT);
-                break;
+        if (blocked) {  // wait on the one unpublished word, then take a fresh window
+            bool gave_up = false;
+            while ((ld_volatile(col + t * kMaxRadix) & kFlagMask) == 0) {
+                if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
+                    set_status(h, PH0_ETIMEOUT);
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(spins < 8 ? 32 : 128);
             }
-            if (spins > 32) __nanosleep(64);
+            if (gave_up) break;
         }
     }
     return excl;
@@ -267,8 +274,6 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
     }
     for (int i = tid; i < W * RADIX / 2; i += T) reinterpret_cast<uint32_t *>(&S.whist[0][0])[i] = 0;
-    if (hist_top)
-        for (int i = tid; i < kMaxRadix; i += T) S.next[i] = 0;
     // bucket starts: exclusive scan of this pass's histogram (thread owns DPT digits)
     uint32_t bucket[DPT], hsum = 0;
 #pragma unroll
@@ -307,38 +312,74 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     for (int j = 0; j < IT; ++j) {
         const uint32_t dj = (bulk || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan)
                                                                    : uint32_t(RADIX);
-        const unsigned peers = __match_any_sync(0xffffffffu, dj);
+        // lanes with the same digit: intersect one ballot per digit bit (much
+        // faster than a warp match on this GPU); the ragged tile's sentinel
+        // digit RADIX needs one more bit
+        unsigned peers = 0xffffffffu;
+        constexpr int kBits = RADIX == 512 ? 9 : 8;
+#pragma unroll
+        for (int b = 0; b < kBits; ++b) {
+            const bool bit = (dj >> b) & 1u;
+            const unsigned vote = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? vote : ~vote;
+        }
+        if (!bulk) {
+            const bool bit = (dj >> kBits) & 1u;
+            const unsigned vote = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? vote : ~vote;
+        }
         const uint32_t before = __popc(peers & lt);
-        const uint32_t prior = dj < RADIX ? S.whist[warp][dj] : 0u;
-        dr[j] = (dj << 16) | (prior + before);
-        __syncwarp();
-        if (dj < RADIX && before == 0) S.whist[warp][dj] = uint16_t(prior + __popc(peers));
-        __syncwarp();
+        if constexpr (RADIX == kMaxRadix) {
+            // 9-bit digits: the leader alone reads and advances its digit's
+            // count and hands it to its peers (measured faster here)
+            const int leader = __ffs(peers) - 1;
+            uint32_t prior = 0;
+            if (before == 0 && dj < RADIX) {
+                prior = S.whist[warp][dj];
+                S.whist[warp][dj] = uint16_t(prior + __popc(peers));
+            }
+            prior = __shfl_sync(0xffffffffu, prior, leader);
+            dr[j] = (dj << 16) | (prior + before);
+            __syncwarp();
+        } else {
+            // 8-bit digits: every lane reads its digit's count, then the leader
+            // advances it (measured faster here)
+            const uint32_t prior = dj < RADIX ? S.whist[warp][dj] : 0u;
+            dr[j] = (dj << 16) | (prior + before);
+            __syncwarp();
+            if (dj < RADIX && before == 0) S.whist[warp][dj] = uint16_t(prior + __popc(peers));
+            __syncwarp();
+        }
     }
     __syncthreads();
 
-    // ---- per digit: warp offsets and tile total; publish the total at once ----
+    // ---- per digit: tile total (published at once), then local positions ----
     uint32_t total[DPT], tsum = 0;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
         uint32_t t = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint32_t c = S.whist[w][d];
-            S.whist[w][d] = uint16_t(t);
-            t += c;
-        }
+        for (int w = 0; w < W; ++w) t += S.whist[w][d];
         total[q] = t;
         tsum += t;
         st_volatile(look + tile * kMaxRadix + d, (tile == 0 ? kFlagPrefix : kFlagAgg) | t);
     }
+    uint32_t lstart[DPT];
     {
         uint32_t tot;
         uint32_t run = block_excl_scan<T>(tsum, S.scan, tot);
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
-            S.lstart[tid * DPT + q] = run;
+            const int d = tid * DPT + q;
+            lstart[q] = run;
+            uint32_t pos = run;  // local position of the first item of each warp, digit d
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = S.whist[w][d];
+                S.whist[w][d] = uint16_t(pos);
+                pos += c;
+            }
             run += total[q];
         }
     }
@@ -350,7 +391,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         const uint32_t dj = dr[j] >> 16;
         const int loc = wloc + j * 32 + lane;
         if (dj < RADIX) {
-            const uint32_t pos = S.lstart[dj] + S.whist[warp][dj] + (dr[j] & 0xffffu);
+            const uint32_t pos = S.whist[warp][dj] + (dr[j] & 0xffffu);
             S.keys[pos] = k[j];
             S.vals[pos] = bulk ? S.vals_in[loc] : vin[base + loc];
         }
@@ -365,7 +406,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             excl = lookback_window(look + d, tile, h);
             st_volatile(look + tile * kMaxRadix + d, kFlagPrefix | uint64_t(excl + total[q]));
         }
-        S.gofs[d] = int64_t(bucket[q]) + excl - int64_t(S.lstart[d]);
+        S.gofs[d] = int32_t(int64_t(bucket[q]) + excl - int64_t(lstart[q]));  // positions < 2^31
+    }
+    uint32_t *s_next = S.vals_in;  // dead once every thread has finished the scatter
+    if (hist_top) {
+        __syncthreads();
+        for (int i = tid; i < kMaxRadix; i += T) s_next[i] = 0;
     }
     __syncthreads();
 
@@ -373,16 +419,16 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 #pragma unroll 4
     for (int i = tid; i < valid; i += T) {
         const uint64_t key = S.keys[i];
-        const int64_t g = S.gofs[slot_digit<SLOT>(key, plan)] + i;
+        const int64_t g = int64_t(S.gofs[slot_digit<SLOT>(key, plan)]) + i;
         kout[g] = key;
         vout[g] = S.vals[i];
         if (hist_top) {
             const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
             if (plan.top == 1) {
-                atomicAdd(&S.next[t], 1u);
+                atomicAdd(&s_next[t], 1u);
             } else {  // two top passes: low and high byte of t
-                atomicAdd(&S.next[t & (kRadix - 1)], 1u);
-                atomicAdd(&S.next[kRadix + (t >> kRadixBits)], 1u);
+                atomicAdd(&s_next[t & (kRadix - 1)], 1u);
+                atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
             }
         }
     }
@@ -390,7 +436,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     if (hist_top) {
         __syncthreads();
         for (int i = tid; i < kMaxRadix; i += T) {
-            const uint32_t c = S.next[i];
+            const uint32_t c = s_next[i];
             if (!c) continue;
             if (plan.top == 1) atomicAdd(&h->hist[SLOT + 1][i], c);
             else atomicAdd(&h->hist[SLOT + 1 + i / kRadix][i % kRadix], c);
