@@ -125,7 +125,7 @@ struct SortSmem {
     uint32_t vals_in[kSortTile];       // input values; after the scatter, the top-digit histogram
     uint32_t vals[kSortTile];          // values in sorted order
     uint16_t whist[W][RADIX];          // counts, then the local position of each warp's first item
-    int32_t gofs[RADIX];               // global position of sorted tile index 0 of each digit's run
+    uint32_t gofs[RADIX];              // global position of sorted tile index 0 of each digit's run (mod 2^32)
     uint32_t scan[W + 1];
     uint32_t tile;
     unsigned long long mbar;           // completion of the tile's bulk copies
@@ -178,40 +178,46 @@ __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p) {
 }
 
 // Decoupled look-back for one digit (column `col` of the per-tile status
-// words, stride kMaxRadix): the sum of the counts of all tiles before `tile`.
-// The PREFIX of the nearest finished predecessor typically lies tens of tiles
-// back, so kLookWindow predecessors are read at once and folded in order;
-// waits on unpublished words are bounded.
+// words, stride kMaxRadix): the sum of the counts of all tiles before `tile`
+// (tile 0's PREFIX also holds the digit's global start).  The PREFIX of the
+// nearest finished predecessor typically lies tens of tiles back, so
+// kLookWindow predecessors are read at once and folded in order; waits on
+// unpublished words are bounded.  Counts and prefixes stay below 2^31, so a
+// word's low half is its count and its high half its flag alone, and an
+// unpublished word is all zero.
 #ifndef PH0_LOOK_WINDOW
 #define PH0_LOOK_WINDOW 16
 #endif
 constexpr int kLookWindow = PH0_LOOK_WINDOW;
-__device__ __forceinline__ int64_t lookback_window(const uint64_t *col, int64_t tile, Header *h) {
-    int64_t excl = 0;
+constexpr uint32_t kHiAgg = uint32_t(kFlagAgg >> 32), kHiPrefix = uint32_t(kFlagPrefix >> 32);
+__device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t tile, Header *h) {
+    uint32_t excl = 0;
     int64_t t = tile - 1;  // next predecessor to fold
     uint32_t spins = 0;
     while (t >= 0) {
-        uint64_t w[kLookWindow];
+        uint32_t lo[kLookWindow], hi[kLookWindow];
 #pragma unroll
-        for (int q = 0; q < kLookWindow; ++q) w[q] = t - q >= 0 ? ld_volatile(col + (t - q) * kMaxRadix) : 0;
-        bool done = false, blocked = false;
+        for (int q = 0; q < kLookWindow; ++q) {
+            const uint64_t w = t - q >= 0 ? ld_volatile(col + (t - q) * kMaxRadix) : 0;
+            lo[q] = uint32_t(w);
+            hi[q] = uint32_t(w >> 32);
+        }
+        // fold AGG words up to the first PREFIX (folded too) or unpublished
+        // word (count 0); past tile 0 nothing is reached, tile 0 being PREFIX
+        bool live = true, done = false;
         int folded = 0;
 #pragma unroll
-        for (int q = 0; q < kLookWindow; ++q) {  // unrolled: w stays in registers
-            if (!done && !blocked && t - q >= 0) {
-                const uint64_t f = w[q] & kFlagMask;
-                if (f == 0) {
-                    blocked = true;  // not published yet: reload from here
-                } else {
-                    excl += int64_t(w[q] & kCountMask);
-                    ++folded;
-                    done = f == kFlagPrefix;
-                }
+        for (int q = 0; q < kLookWindow; ++q) {
+            if (live) {
+                excl += lo[q];
+                done = hi[q] == kHiPrefix;
+                live = hi[q] == kHiAgg;
+                folded += live;
             }
         }
         if (done) break;
         t -= folded;
-        if (blocked) {  // wait on the one unpublished word, then take a fresh window
+        if (!live) {  // an unpublished word: wait on it, then take a fresh window
             bool gave_up = false;
             while ((ld_volatile(col + t * kMaxRadix) & kFlagMask) == 0) {
                 if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
@@ -242,6 +248,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     constexpr int T = kSortThreads, IT = kSortItems, TILE = kSortTile, W = T / 32;
     constexpr int DPT = RADIX / T;  // digits per thread
     static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
+    static_assert((TILE & (TILE - 1)) == 0, "tile positions are masked to the tile");
     extern __shared__ __align__(16) unsigned char s_raw[];
     SortSmem<RADIX> &S = *reinterpret_cast<SortSmem<RADIX> *>(s_raw);
 
@@ -273,15 +280,24 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         bulk_g2s(S.keys, kin + base, uint32_t(TILE * sizeof(uint64_t)), &S.mbar);
         bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
     }
-    for (int i = tid; i < W * RADIX / 2; i += T) reinterpret_cast<uint32_t *>(&S.whist[0][0])[i] = 0;
-    // bucket starts: exclusive scan of this pass's histogram (thread owns DPT digits)
-    uint32_t bucket[DPT], hsum = 0;
+    {  // each warp clears its own counter row (ranking touches only that row)
+        uint32_t *row = reinterpret_cast<uint32_t *>(&S.whist[warp][0]);
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) {
-        bucket[q] = h->hist[SLOT][tid * DPT + q];
-        hsum += bucket[q];
+        for (int i = lane; i < RADIX / 2; i += 32) row[i] = 0;
+        __syncwarp();
     }
-    {
+    // digit starts (tile 0 only): exclusive scan of this pass's histogram;
+    // tile 0 folds them into its PREFIX, so later tiles get them by look-back
+    uint32_t bucket[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) bucket[q] = 0;
+    if (tile == 0) {
+        uint32_t hsum = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            bucket[q] = h->hist[SLOT][tid * DPT + q];
+            hsum += bucket[q];
+        }
         uint32_t tot;
         uint32_t run = block_excl_scan<T>(hsum, S.scan, tot);
 #pragma unroll
@@ -363,7 +379,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         for (int w = 0; w < W; ++w) t += S.whist[w][d];
         total[q] = t;
         tsum += t;
-        st_volatile(look + tile * kMaxRadix + d, (tile == 0 ? kFlagPrefix : kFlagAgg) | t);
+        st_volatile(look + tile * kMaxRadix + d, tile == 0 ? kFlagPrefix | (bucket[q] + t) : kFlagAgg | t);
     }
     uint32_t lstart[DPT];
     {
@@ -391,7 +407,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         const uint32_t dj = dr[j] >> 16;
         const int loc = wloc + j * 32 + lane;
         if (dj < RADIX) {
-            const uint32_t pos = S.whist[warp][dj] + (dr[j] & 0xffffu);
+            const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
             S.keys[pos] = k[j];
             S.vals[pos] = bulk ? S.vals_in[loc] : vin[base + loc];
         }
@@ -401,12 +417,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
-        int64_t excl = 0;
+        uint32_t excl = bucket[q];
         if (tile != 0) {
             excl = lookback_window(look + d, tile, h);
             st_volatile(look + tile * kMaxRadix + d, kFlagPrefix | uint64_t(excl + total[q]));
         }
-        S.gofs[d] = int32_t(int64_t(bucket[q]) + excl - int64_t(lstart[q]));  // positions < 2^31
+        S.gofs[d] = excl - lstart[q];  // wraps below 0; positions are < 2^31
     }
     uint32_t *s_next = S.vals_in;  // dead once every thread has finished the scatter
     if (hist_top) {
@@ -416,10 +432,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     __syncthreads();
 
     // ---- write contiguous runs, one per digit ----
+    const uint32_t m32 = uint32_t(m);  // m < 2^31
 #pragma unroll 4
     for (int i = tid; i < valid; i += T) {
         const uint64_t key = S.keys[i];
-        const int64_t g = int64_t(S.gofs[slot_digit<SLOT>(key, plan)]) + i;
+        const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan)] + uint32_t(i);
+        if (g >= m32) continue;  // never taken when the counts are consistent
         kout[g] = key;
         vout[g] = S.vals[i];
         if (hist_top) {
