@@ -456,29 +456,51 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     }
 }
 
-// One thread per bar: the killing edge, its index a in D, its pivot row, its
-// position, and the death value sqrt(d2) (IEEE round to nearest).
+// One warp per bar: the killing edge, its index a in D, its pivot row, its
+// position, and the death value sqrt(d2) (IEEE round to nearest).  a comes
+// from the caller's per-edge array, or (a == null) from the de-duplication
+// scan's chunk prefix plus the new values of p's chunk up to p.
 __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                        const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                        const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                        const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                       ph0_bar *bars) {
-    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+                       const uint32_t *cpref, ph0_bar *bars) {
+    const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
+    const int lane = threadIdx.x & 31;
     if (j >= nb) return;
     const bool kodd = kill_h && (make_plan(kill_h).passes & 1);
     const bool sodd = sort_h && (make_plan(sort_h).passes & 1);
     const unsigned long long p = kodd ? kk1[j] : kk0[j];
     const uint32_t low = kodd ? kv1[j] : kv0[j];
     if (p >= (unsigned long long)m) {  // fewer pivots than n-1: only after a reported error
-        set_status(h, PH0_EINTERNAL);
+        if (lane == 0) set_status(h, PH0_EINTERNAL);
         return;
     }
+    const uint64_t *keys = sodd ? key1 : key0;
+    uint32_t aval;
+    if (a) {
+        aval = a[p];
+    } else {
+        constexpr int kPer = kDedupeChunk / 32;
+        const int64_t c0 = int64_t(p) & ~int64_t(kDedupeChunk - 1);
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int64_t i = c0 + lane * kPer + q;
+            if (i <= int64_t(p)) {
+                const uint64_t k = keys[i];
+                cnt += i == 0 || k != keys[i - 1];
+            }
+        }
+        aval = cpref[c0 / kDedupeChunk] + __reduce_add_sync(0xffffffffu, cnt);
+    }
+    if (lane != 0) return;
     const uint32_t vv = sodd ? val1[p] : val0[p];
-    const uint64_t key = sodd ? key1[p] : key0[p];
+    const uint64_t key = keys[p];
     ph0_bar b;
     b.u = int32_t(vv >> 16);
     b.v = int32_t(vv & 0xffffu);
-    b.a = a[p];
+    b.a = aval;
     b.low = int32_t(low);
     b.order = int64_t(p);
     b.death_sq = __longlong_as_double((long long)key);
@@ -526,10 +548,10 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        ph0_bar *bars, cudaStream_t s) {
+                        const uint32_t *cpref, ph0_bar *bars, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
-    k_emit<<<unsigned((nb + 255) / 256), 256, 0, s>>>(nb, m, h, kk0, kk1, kv0, kv1, kill_h, val0, val1, key0,
-                                                     key1, sort_h, a, bars);
+    k_emit<<<unsigned((nb + 7) / 8), 256, 0, s>>>(nb, m, h, kk0, kk1, kv0, kv1, kill_h, val0, val1, key0,
+                                                 key1, sort_h, a, cpref, bars);
     return cudaGetLastError();
 }
 

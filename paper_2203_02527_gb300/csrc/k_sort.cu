@@ -189,7 +189,6 @@ __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p) {
 #define PH0_LOOK_WINDOW 16
 #endif
 constexpr int kLookWindow = PH0_LOOK_WINDOW;
-constexpr uint32_t kHiAgg = uint32_t(kFlagAgg >> 32), kHiPrefix = uint32_t(kFlagPrefix >> 32);
 __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t tile, Header *h) {
     uint32_t excl = 0;
     int64_t t = tile - 1;  // next predecessor to fold

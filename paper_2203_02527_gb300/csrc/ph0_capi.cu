@@ -25,7 +25,8 @@ cudaError_t prepare_sort_kernels();
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
-                          int64_t m, uint32_t *a, uint64_t *look, Header *h, cudaStream_t s);
+                          int64_t m, uint32_t *a, uint32_t *cpref, uint64_t *look, Header *h,
+                          cudaStream_t s);
 cudaError_t launch_backward(const float *pts, int64_t n, int32_t d, int64_t ld, const ph0_bar *bars,
                             int64_t nb, const double *dl, float *grad, double *acc, cudaStream_t s);
 
@@ -34,7 +35,7 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        ph0_bar *bars, cudaStream_t s);
+                        const uint32_t *cpref, ph0_bar *bars, cudaStream_t s);
 
 namespace {
 
@@ -75,12 +76,14 @@ cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s, int top_bits =
 }
 
 // Steps 4-5 plus the read-out: reduce, order the pivot columns by position,
-// emit the bars.  val/key/a are either the workspace's ping-pong buffers
-// (sort_h != null selects the one holding the sorted data) or the caller's.
+// emit the bars.  val/key are either the workspace's ping-pong buffers
+// (sort_h != null selects the one holding the sorted data) or the caller's;
+// a is the caller's per-edge index, or null with cpref the workspace's chunk
+// prefixes of the count-mode scan.
 cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
                             const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
-                            const Header *sort_h, const uint32_t *a, ph0_bar *bars, cudaStream_t s,
-                            cudaEvent_t after_reduce = nullptr) {
+                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
+                            ph0_bar *bars, cudaStream_t s, cudaEvent_t after_reduce = nullptr) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t m = n_edges(n);
     ReduceArgs A;
@@ -126,7 +129,7 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
     if (e != cudaSuccess) return e;
     return launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
                        reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
-                       key0, key1, sort_h, a, bars, s);
+                       key0, key1, sort_h, a, cpref, bars, s);
 }
 
 }  // namespace
@@ -171,14 +174,14 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
-    uint32_t *a = at<uint32_t>(ws, L.a);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess)
         e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
                                at<uint64_t>(ws, L.look[1]), h, s);
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     return cuda_status(e);
 }
 
@@ -200,7 +203,7 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
-    uint32_t *a = at<uint32_t>(ws, L.a);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
     constexpr int kEv = 6 + kMaxPasses;
     cudaEvent_t ev[kEv];
@@ -223,9 +226,9 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
         if (L.m > 0) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
     }
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s, ev[3 + kMaxPasses]);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s, ev[3 + kMaxPasses]);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4 + kMaxPasses], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[4 + kMaxPasses]);
     if (e == cudaSuccess) {
@@ -337,7 +340,7 @@ int ph0_dedupe(const uint64_t *key_sorted_dev, int64_t m, uint32_t *a_dev, void 
     Header *h = at<Header>(ws, L.hdr);
     cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
     if (e == cudaSuccess)
-        e = launch_dedupe(key_sorted_dev, key_sorted_dev, nullptr, m, a_dev, at<uint64_t>(ws, L.dlook), h, s);
+        e = launch_dedupe(key_sorted_dev, key_sorted_dev, nullptr, m, a_dev, nullptr, at<uint64_t>(ws, L.dlook), h, s);
     return cuda_status(e);
 }
 
@@ -355,7 +358,7 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev, const uint32_t *a_dev,
     cudaError_t e = cudaMemsetAsync(at<Header>(ws, L.hdr), 0, kHeaderBytes, s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, val_sorted_dev, val_sorted_dev, key_sorted_dev, key_sorted_dev,
-                            nullptr, a_dev, bars_dev, s);
+                            nullptr, a_dev, nullptr, bars_dev, s);
     return cuda_status(e);
 }
 
@@ -424,7 +427,7 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
-    uint32_t *a = at<uint32_t>(ws, L.a);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     // the array keeps the previous call's contents: begin_call zeroes the
     // header and the first look-back buffer, and every later stage clears or
     // overwrites what it reads before reading it
@@ -433,8 +436,8 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     if (e == cudaSuccess)
         e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
                                at<uint64_t>(ws, L.look[1]), h, s);
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, a, at<uint64_t>(ws, L.dlook), h, s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, a, bars_dev, s);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int32_t status = PH0_OK;
     if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);

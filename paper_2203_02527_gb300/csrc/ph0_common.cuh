@@ -39,6 +39,9 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kFlagMask = 3ull << 62;
 constexpr uint64_t kCountMask = ~kFlagMask;
+// Counts and prefixes stay below 2^31, so a status word's high half holds its
+// flag alone and its low half its count; an unpublished word is all zero.
+constexpr uint32_t kHiAgg = uint32_t(kFlagAgg >> 32), kHiPrefix = uint32_t(kFlagPrefix >> 32);
 
 // --------------------------------------------------------------- header ---
 // Lives at offset 0 of the workspace.  Every counter the kernels share.
@@ -86,6 +89,8 @@ constexpr int kTraceWindows = 256;
 constexpr int kTraceWords = 12;
 // Candidate count at or below which one CTA finishes a window in shared memory.
 constexpr int kTailCap = 2048;
+// Keys per chunk of the de-duplication scan's count mode (one prefix each).
+constexpr int kDedupeChunk = 256;
 
 // Byte offsets of every region of the workspace for a cloud of n points in
 // dimension d.  Everything is caller-owned device memory; nothing is
@@ -93,7 +98,8 @@ constexpr int kTailCap = 2048;
 struct Layout {
     int64_t n, m, tiles, ktiles;
     size_t hdr, aux_hdr;                 // main header, header of the small sorts
-    size_t key[2], val[2], a, look[2];   // edge records, ping-pong, look-back words
+    size_t key[2], val[2], look[2];      // edge records, ping-pong, look-back words
+    size_t cpref;                        // de-duplication prefix of every key chunk
     size_t dlook;                        // look-back words of the de-duplication scan
     size_t comp, parent, res, cand[2], candr;
     size_t kill_key[2], kill_val[2], kill_look[2];
@@ -118,7 +124,7 @@ struct Layout {
         key[1] = take(8 * size_t(m));
         val[0] = take(4 * size_t(m));
         val[1] = take(4 * size_t(m));
-        a = take(4 * size_t(m));
+        cpref = take(4 * size_t((m + kDedupeChunk - 1) / kDedupeChunk + 1));
         look[0] = take(8 * size_t(tiles) * kMaxRadix);
         look[1] = take(8 * size_t(tiles) * kMaxRadix);
         dlook = take(8 * size_t(tiles + 1));
