@@ -16,7 +16,8 @@
 // digit, publishes its per-digit counts, and obtains the counts of all
 // earlier tiles by decoupled look-back over per-tile status words.  Ranking
 // finds the lanes of a warp that share a digit by intersecting one warp
-// ballot per digit bit.  The tile is reordered by digit in shared memory and
+// ballot per digit bit (8-bit digits) or by one warp match (the 9-bit top
+// digit, which is concentrated on few values).  The tile is reordered by digit in shared memory and
 // written out as contiguous runs, one run per digit.  The six low-digit
 // histograms come from the distance kernel; the last low pass histograms the
 // top digit(s) while it writes, so no pass needs an extra read of the keys.
@@ -327,21 +328,28 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     for (int j = 0; j < IT; ++j) {
         const uint32_t dj = (bulk || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan)
                                                                    : uint32_t(RADIX);
-        // lanes with the same digit: intersect one ballot per digit bit (much
-        // faster than a warp match on this GPU); the ragged tile's sentinel
-        // digit RADIX needs one more bit
+        // lanes with the same digit.  8-bit digits (raw mantissa bytes, about
+        // uniform: a warp holds ~30 distinct values): intersect one ballot per
+        // digit bit, much faster than a warp match on this GPU; the ragged
+        // tile's sentinel digit RADIX needs one more bit.  The 9-bit top digit
+        // (exponent and leading mantissa bits of d2) is concentrated on few
+        // values, where one warp match beats nine ballots.
         unsigned peers = 0xffffffffu;
-        constexpr int kBits = RADIX == 512 ? 9 : 8;
+        if constexpr (RADIX == kMaxRadix) {
+            peers = __match_any_sync(0xffffffffu, dj);
+        } else {
+            constexpr int kBits = 8;
 #pragma unroll
-        for (int b = 0; b < kBits; ++b) {
-            const bool bit = (dj >> b) & 1u;
-            const unsigned vote = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? vote : ~vote;
-        }
-        if (!bulk) {
-            const bool bit = (dj >> kBits) & 1u;
-            const unsigned vote = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? vote : ~vote;
+            for (int b = 0; b < kBits; ++b) {
+                const bool bit = (dj >> b) & 1u;
+                const unsigned vote = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? vote : ~vote;
+            }
+            if (!bulk) {
+                const bool bit = (dj >> kBits) & 1u;
+                const unsigned vote = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? vote : ~vote;
+            }
         }
         const uint32_t before = __popc(peers & lt);
         if constexpr (RADIX == kMaxRadix) {
