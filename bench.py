@@ -32,10 +32,11 @@ from paper_2203_02527_gb300 import inputs  # noqa: E402
 from paper_2203_02527_gb300.replicas import job_throughput, max_over_ranks, replica_seed  # noqa: E402
 
 WORKLOAD = "circles32768"
-# DRAM bytes per edge of one low radix pass (dram__bytes_read.sum +
-# dram__bytes_write.sum of k_onesweep<256, 0..3> on the 8192-point cloud,
-# profiles/kernels_circles8192.md), scaled by edges to a full launch.
-ONESWEEP_TRAFFIC_PER_EDGE = 23.96
+# DRAM bytes per edge of one radix pass, averaged over the seven passes
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_onesweep on the
+# 8192-point cloud, profiles/kernels_circles8192.md), scaled by edges to a
+# full launch.
+ONESWEEP_TRAFFIC_PER_EDGE = 24.49
 METRIC = "edges sorted+reduced/s at N=32768"
 # bounded sample of the workload for the CPU oracle: every 5th point
 SAMPLE_STRIDE = 5
@@ -175,7 +176,7 @@ def run_ours(args, rank, world, local_rank):
     tuning = None
     if not args.no_tune:
         from paper_2203_02527_gb300 import autotune
-        tuning = autotune.tune(d, n=min(n, 8192))  # cached for ph0.barcodes below
+        tuning = autotune.tune(d, n=n)  # cached for ph0.barcodes below
     ws = ph0.Workspace(n, d, dev)
     bars = torch.empty((n - 1, 40), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
@@ -250,7 +251,9 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
                 "traffic_source": "ncu on the 8192-point cloud, scaled by edges",
                 "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src}
-    launches_per_step = 2 + 1 + 8 + 1 + 2 + 2 + 8 + 1  # init, dist, passes, dedupe, reduce, kill sort, emit
+    # sort inits, distances, radix passes, de-duplication (count, scan), reduction
+    # (init, kernel), pivot-order sort (key stats, passes), emission
+    launches_per_step = 2 + 1 + 8 + 2 + 2 + 1 + 8 + 1
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         r, dt, ns, ms_ = time_oracle(x)

@@ -7,8 +7,9 @@ ph0_barcodes_profiled) and keeps the fastest:
                      sums on the binary64 units (the rest all in integers),
   * dist_tile     -- points per side of a distance tile (32, 64, 128),
   * sort_top_bits -- width of the single top radix pass (8 or 9).
-Results are cached in a JSON file keyed by GPU name and dimension bucket
-($PH0_TUNING_CACHE, default ~/.cache/ph0_gb300/tuning.json).  No setting
+Results are cached in a JSON file keyed by GPU name, dimension bucket and
+cloud-size bucket ($PH0_TUNING_CACHE, default ~/.cache/ph0_gb300/tuning.json):
+the best distance tile depends on how many tiles a cloud has to fill the GPU.  No setting
 changes any result bit; ph0.barcodes uses the cached choice when present.
 """
 from __future__ import annotations
@@ -28,6 +29,20 @@ def bucket(d: int) -> int:
         if d <= b:
             return b
     return BUCKETS[-1]
+
+
+N_BUCKETS = (2048, 8192, 24576, 65535)
+
+
+def n_bucket(n: int) -> int:
+    for b in N_BUCKETS:
+        if n <= b:
+            return b
+    return N_BUCKETS[-1]
+
+
+def _key(d: int, n: int) -> str:
+    return f"{_device_key()}/d{bucket(d)}/n{n_bucket(n)}"
 
 
 def cache_path() -> str:
@@ -52,19 +67,19 @@ def _load():
     return _cache
 
 
-def cached(d: int):
-    """The cached tuning for dimension d on this GPU, or None."""
+def cached(d: int, n: int):
+    """The cached tuning for an n-point cloud of dimension d on this GPU, or None."""
     try:
-        key = f"{_device_key()}/d{bucket(d)}"
+        key = _key(d, n)
     except Exception:
         return None
     return _load().get(key)
 
 
-def _store(d: int, tuning: dict):
+def _store(d: int, n: int, tuning: dict):
     c = _load()
     with _lock:
-        c[f"{_device_key()}/d{bucket(d)}"] = tuning
+        c[_key(d, n)] = tuning
         path = cache_path()
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"
@@ -75,7 +90,7 @@ def _store(d: int, tuning: dict):
 
 def tune(d: int, n: int = 8192, repeats: int = 3, seed: int = 7, verbose: bool = False) -> dict:
     """Measure the candidates for dimension d on an n-point cloud; cache and
-    return the fastest setting."""
+    return the fastest setting (for clouds of n's size bucket)."""
     import torch
 
     from . import inputs, ph0
@@ -108,5 +123,5 @@ def tune(d: int, n: int = 8192, repeats: int = 3, seed: int = 7, verbose: bool =
     if verbose:
         print({"d": d, "dist_ms": {f"{k[0]}/{k[1]}": v for k, v in dist.items()},
                "sort_ms": sort, "chosen": chosen})
-    _store(d, chosen)
+    _store(d, n, chosen)
     return chosen

@@ -93,13 +93,13 @@ def _points(pts: torch.Tensor):
     return pts, pts.shape[0], pts.shape[1], pts.stride(0)
 
 
-def _tuning(d: int, tuning):
-    """Explicit tuning, else the autotuner's cached choice for this dimension
-    (None: the library's built-in choice)."""
+def _tuning(n: int, d: int, tuning):
+    """Explicit tuning, else the autotuner's cached choice for this cloud size
+    and dimension (None: the library's built-in choice)."""
     if tuning is not None:
         return tuning if isinstance(tuning, _lib.Tuning) else _lib.Tuning.make(**tuning)
     from . import autotune
-    t = autotune.cached(d)
+    t = autotune.cached(d, n)
     return _lib.Tuning.make(**t) if t else None
 
 
@@ -111,7 +111,7 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     s = _stream()
     lib = _lib.load()
-    t = _tuning(d, tuning)
+    t = _tuning(n, d, tuning)
     check(lib.ph0_barcodes_tuned(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, s,
                                  ctypes.byref(t) if t is not None else None), "ph0_barcodes")
     st = None
@@ -129,7 +129,7 @@ def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torc
     if bars is None:
         bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     prof = _lib.Profile()
-    t = _tuning(d, tuning)
+    t = _tuning(n, d, tuning)
     check(_lib.load().ph0_barcodes_profiled(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes,
                                             _stream(), ctypes.byref(t) if t is not None else None,
                                             ctypes.byref(prof)), "ph0_barcodes_profiled")

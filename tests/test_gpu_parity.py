@@ -191,4 +191,4 @@ def test_autotuner_picks_valid_settings(tmp_path, monkeypatch):
     t = autotune.tune(3, n=1024, repeats=1)
     assert t["dist_split16"] in (0, 4, 8, 12, 16)
     assert t["dist_tile"] in (64, 128) and t["sort_top_bits"] in (8, 9)
-    assert autotune.cached(3) == t
+    assert autotune.cached(3, 1024) == t
