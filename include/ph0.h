@@ -83,6 +83,9 @@ typedef struct {
     int64_t n_bars;          /* finite bars written                           */
     int64_t dist_tiles;      /* distance tiles                                */
     int64_t dist_tiles_int;  /* ... of which computed on the integer path     */
+    int64_t sorted_edges;    /* edges sorted: n(n-1)/2, or the prefix sorted by
+                                ph0_barcodes_early (n_distinct then counts the
+                                distinct values of that prefix)               */
 } ph0_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -116,6 +119,24 @@ typedef struct {
                                part takes two passes of 8); built-in 9                   */
     int32_t reserved[5];
 } ph0_tuning;
+
+/* Early-terminating whole path (the paper has no counterpart; it exploits
+ * that the reduction of Sec. 2 reads the sorted edges only up to the last
+ * killing edge).  Same arguments and results as ph0_barcodes(), bit for bit:
+ * the same n-1 bars (killing edges, positions `order` in the full sorted
+ * edge list, indices a, deaths).  Instead of sorting all n(n-1)/2 edges it
+ * sorts a prefix of the edge order: it histograms the squared distances,
+ * partitions the edges stably into classes of consecutive distance ranges
+ * (the first 2%, 8%, 25%, 45% of the edges, cumulative, then the rest), then
+ * sorts one class after the other into the prefix and runs the reduction on
+ * the prefix, until it holds n-1 pivots.  The prefix holds every killing
+ * edge exactly when the reduction finds n-1 pivots in it, so the result
+ * never differs.  Synchronous: waits for `stream` between rounds and returns the
+ * device status (as ph0_finish() would); ph0_finish() reports the prefix
+ * length in sorted_edges.  Fastest when the last killing edge comes early in
+ * the edge order (clustered or uniform clouds). */
+int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                       ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
 
 /* ph0_barcodes() with explicit tuning (NULL = built-in). */
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,

@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
         ("n_distinct", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
         ("candidates", ctypes.c_int64), ("rounds", ctypes.c_int64),
         ("n_bars", ctypes.c_int64), ("dist_tiles", ctypes.c_int64),
-        ("dist_tiles_int", ctypes.c_int64),
+        ("dist_tiles_int", ctypes.c_int64), ("sorted_edges", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -105,6 +105,7 @@ SIGNATURES = {
     "ph0_abi_version": (ctypes.c_int32, []),
     "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
     "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
+    "ph0_barcodes_early": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
     "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
                                           ctypes.POINTER(Tuning)]),

@@ -31,7 +31,7 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
     constexpr int T = kDedupeThreads, IT = kDedupeItems, TILE = kDedupeTile, NW = T / 32;
     __shared__ uint64_t s_key[TILE + 1];
     __shared__ uint32_t s_cnt[IT * NW];  // new-value count per (item row, warp), then offsets
-    __shared__ uint32_t s_tile, s_total, s_excl;
+    __shared__ uint32_t s_tile, s_excl;
 
     const uint64_t *keys = keys0;
     if (sort_h) keys = (make_plan(sort_h).passes & 1) ? keys1 : keys0;
@@ -132,7 +132,6 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
         }
         if (lane == 0) {
             s_excl = excl;
-            s_total = total;
             if (base + valid == m) h->n_distinct = int64_t(excl) + total;
         }
     }

@@ -57,10 +57,12 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp
 }
 
 // Header fields a sort needs zeroed: histograms, key range, tile counters.
-__global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int top_bits) {
+__global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int top_bits,
+                            int64_t sorted_edges) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     if (tid == 0) {
+        if (sorted_edges >= 0) h->sorted_edges = sorted_edges;
         h->kmin = ~0ull;
         h->kmax = 0;
         h->sort_passes = 0;
@@ -153,6 +155,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+// Per-thread asynchronous copies global -> shared (the source only needs the
+// alignment of the copy size): a full tile whose rows are not 16-byte aligned.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Bounded wait for phase `parity` of the barrier; false on timeout.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
@@ -170,12 +182,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
 // Digit of a key in pass slot SLOT: slots 0..5 are the raw bytes of bits
 // 0..47; slot 6 is the top part (all of it if it has at most 9 bits, else its
 // low byte); slot 7 is the high byte of a 16-bit top part.
+// Slot kClassSlot (the early path's partition): the class of the key's bin,
+// the number of class bounds bound[1..nc-1] at or below the bin.
+struct ClassDigit {
+    uint64_t kmin;
+    int shift, nc;
+    const uint32_t *bound;  // shared memory
+};
 template <int SLOT>
-__device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p) {
-    if (SLOT < kLowPasses) return uint32_t(key >> (kRadixBits * SLOT)) & (kRadix - 1);
-    const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
-    if (SLOT == kLowPasses) return p.top == 1 ? t : (t & (kRadix - 1));
-    return t >> kRadixBits;
+__device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p, const ClassDigit &cd) {
+    if constexpr (SLOT == kClassSlot) {
+        const uint32_t bin = uint32_t((key - cd.kmin) >> cd.shift);
+        uint32_t c = 0;
+#pragma unroll
+        for (int q = 1; q < kPrefixClasses; ++q) c += (q < cd.nc && bin >= cd.bound[q]) ? 1u : 0u;
+        return c;
+    } else {
+        if (SLOT < kLowPasses) return uint32_t(key >> (kRadixBits * SLOT)) & (kRadix - 1);
+        const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+        if (SLOT == kLowPasses) return p.top == 1 ? t : (t & (kRadix - 1));
+        return t >> kRadixBits;
+    }
 }
 
 // Decoupled look-back for one digit (column `col` of the per-tile status
@@ -241,7 +268,7 @@ __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t
 // buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
 // pass's radix) live in look[p&1], and it clears its tile's words in
 // look[(p+1)&1] for the next pass (whose previous user, pass p-1, is done).
-template <int RADIX, int SLOT>
+template <int RADIX, int SLOT, bool ALIGNED>
 __global__ void __launch_bounds__(kSortThreads, PH0_SORT_MIN_BLOCKS)
 k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
            uint64_t *look0, uint64_t *look1, Header *h) {
@@ -253,32 +280,51 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     SortSmem<RADIX> &S = *reinterpret_cast<SortSmem<RADIX> *>(s_raw);
 
     const Plan plan = make_plan(h);
-    if (SLOT >= plan.passes) return;
+    if (SLOT != kClassSlot && SLOT >= plan.passes) return;
     const uint64_t *kin = (SLOT & 1) ? keys1 : keys0;
     uint64_t *kout = (SLOT & 1) ? keys0 : keys1;
     const uint32_t *vin = (SLOT & 1) ? vals1 : vals0;
     uint32_t *vout = (SLOT & 1) ? vals0 : vals1;
     uint64_t *look = (SLOT & 1) ? look1 : look0;
     uint64_t *look_next = (SLOT & 1) ? look0 : look1;
-    const bool hist_top = plan.top > 0 && SLOT == plan.low - 1;
+    const bool hist_top = SLOT != kClassSlot && plan.top > 0 && SLOT == plan.low - 1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         S.tile = atomicAdd(&h->tile_counter[SLOT], 1u);
         mbar_init(&S.mbar, 1);
     }
+    ClassDigit cd{};
+    if constexpr (SLOT == kClassSlot) {
+        __shared__ uint32_t s_bound[kPrefixClasses + 1];
+        if (tid <= kPrefixClasses) s_bound[tid] = h->part_bound[tid];
+        cd = ClassDigit{h->part_kmin, h->part_shift, h->part_nc, s_bound};
+    }
     __syncthreads();
     const int64_t tile = S.tile;
     const int64_t base = tile * TILE;
     const int valid = int(m - base < TILE ? m - base : TILE);
-    // full tiles with 16-byte aligned rows arrive by two bulk copies that
-    // overlap the histogram scan below; the ragged last tile uses plain loads
+    // full tiles arrive in shared memory while the histogram scan below runs:
+    // by two bulk copies when their rows are 16-byte aligned, else (an
+    // instance for unaligned buffers) by each thread's asynchronous copies of
+    // its own items; the ragged last tile uses plain loads
     const bool bulk = valid == TILE &&
                       ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15u) == 0;
+    const bool full = ALIGNED ? bulk : valid == TILE;
     if (bulk && tid == 0) {
         mbar_expect_tx(&S.mbar, uint32_t(TILE * (sizeof(uint64_t) + sizeof(uint32_t))));
         bulk_g2s(S.keys, kin + base, uint32_t(TILE * sizeof(uint64_t)), &S.mbar);
         bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
+    }
+    if constexpr (!ALIGNED) {
+        if (full && !bulk) {
+            const int own = warp * 32 * IT + lane;
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                cp_async8(&S.keys[own + j * 32], kin + base + own + j * 32);
+                cp_async4(&S.vals_in[own + j * 32], vin + base + own + j * 32);
+            }
+        }
     }
     {  // each warp clears its own counter row (ranking touches only that row)
         uint32_t *row = reinterpret_cast<uint32_t *>(&S.whist[warp][0]);
@@ -295,7 +341,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         uint32_t hsum = 0;
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
-            bucket[q] = h->hist[SLOT][tid * DPT + q];
+            bucket[q] = h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
             hsum += bucket[q];
         }
         uint32_t tot;
@@ -312,8 +358,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     uint64_t k[IT];
     uint32_t dr[IT];  // digit << 16 | rank within the warp, then the local position
     const int wloc = warp * 32 * IT;  // the warp's first item within the tile
-    if (bulk) {
-        if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
+    if (full) {  // each thread reads (and later scatters) only its own items
+        if (bulk) {
+            if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
+        } else {
+            cp_async_wait_all();
+        }
 #pragma unroll
         for (int j = 0; j < IT; ++j) k[j] = S.keys[wloc + j * 32 + lane];
     } else {
@@ -326,7 +376,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
-        const uint32_t dj = (bulk || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan)
+        const uint32_t dj = (full || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan, cd)
                                                                    : uint32_t(RADIX);
         // lanes with the same digit.  8-bit digits (raw mantissa bytes, about
         // uniform: a warp holds ~30 distinct values): intersect one ballot per
@@ -345,7 +395,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
                 const unsigned vote = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? vote : ~vote;
             }
-            if (!bulk) {
+            if (!full) {
                 const bool bit = (dj >> kBits) & 1u;
                 const unsigned vote = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? vote : ~vote;
@@ -416,7 +466,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         if (dj < RADIX) {
             const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
             S.keys[pos] = k[j];
-            S.vals[pos] = bulk ? S.vals_in[loc] : vin[base + loc];
+            S.vals[pos] = full ? S.vals_in[loc] : vin[base + loc];
         }
     }
 
@@ -443,7 +493,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 #pragma unroll 4
     for (int i = tid; i < valid; i += T) {
         const uint64_t key = S.keys[i];
-        const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan)] + uint32_t(i);
+        const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan, cd)] + uint32_t(i);
         if (g >= m32) continue;  // never taken when the counts are consistent
         kout[g] = key;
         vout[g] = S.vals[i];
@@ -463,8 +513,9 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         for (int i = tid; i < kMaxRadix; i += T) {
             const uint32_t c = s_next[i];
             if (!c) continue;
-            if (plan.top == 1) atomicAdd(&h->hist[SLOT + 1][i], c);
-            else atomicAdd(&h->hist[SLOT + 1 + i / kRadix][i % kRadix], c);
+            constexpr int kNext = SLOT + 1 < kMaxPasses ? SLOT + 1 : kMaxPasses - 1;  // class slot: never
+            if (plan.top == 1) atomicAdd(&h->hist[kNext][i], c);
+            else atomicAdd(&h->hist[kNext + i / kRadix][i % kRadix], c);
         }
     }
     if (tile == 0 && tid == 0) {
@@ -498,12 +549,13 @@ int sm_count() {
 }
 
 // Zero the sort's counters and first look-back buffer (sized for 512 buckets).
-cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s, int top_bits) {
+cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s, int top_bits,
+                             int64_t sorted_edges) {
     const int64_t words = tiles * kMaxRadix;
     int blocks = int((words + 255) / 256);
     if (blocks < 8) blocks = 8;
     if (blocks > 4 * sm_count() * 8) blocks = 4 * sm_count() * 8;
-    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words, top_bits == 8 ? 8 : 9);
+    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words, top_bits == 8 ? 8 : 9, sorted_edges);
     return cudaGetLastError();
 }
 
@@ -518,7 +570,10 @@ cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStre
 
 template <int RADIX, int SLOT>
 static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_onesweep<RADIX, SLOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(sort_smem<RADIX>()));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(sort_smem<RADIX>()));
 }
 
@@ -532,14 +587,22 @@ cudaError_t prepare_sort_kernels() {
     if (e == cudaSuccess) e = set_attr<kRadix, 5>();
     if (e == cudaSuccess) e = set_attr<kMaxRadix, 6>();
     if (e == cudaSuccess) e = set_attr<kRadix, 7>();
+    if (e == cudaSuccess) e = set_attr<kRadix, kClassSlot>();
     return e;
 }
 
 template <int RADIX, int SLOT>
 static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                         int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s) {
-    k_onesweep<RADIX, SLOT><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1, m,
-                                                                             look0, look1, h);
+    // tiles arrive by bulk copies only when both buffers' rows are 16-byte aligned
+    const bool aligned = ((reinterpret_cast<uintptr_t>(keys0) | reinterpret_cast<uintptr_t>(keys1) |
+                           reinterpret_cast<uintptr_t>(vals0) | reinterpret_cast<uintptr_t>(vals1)) & 15u) == 0;
+    if (aligned)
+        k_onesweep<RADIX, SLOT, true><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1,
+                                                                                     m, look0, look1, h);
+    else
+        k_onesweep<RADIX, SLOT, false><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1,
+                                                                                      m, look0, look1, h);
 }
 
 // One pass slot (prepare_sort_kernels() must have run).
@@ -555,7 +618,8 @@ cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, 
         case 4: launch_slot<kRadix, 4>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
         case 5: launch_slot<kRadix, 5>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
         case 6: launch_slot<kMaxRadix, 6>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        default: launch_slot<kRadix, 7>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 7: launch_slot<kRadix, 7>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        default: launch_slot<kRadix, kClassSlot>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
     }
     return cudaGetLastError();
 }

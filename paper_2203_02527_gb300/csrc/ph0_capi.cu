@@ -1,10 +1,12 @@
 // ph0_capi.cu -- the C ABI of libph0 (declared in include/ph0.h): argument
 // checks, workspace carving and kernel launches for the five steps of the
-// barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).  No allocation, no global
-// state: every buffer is caller-owned and every call is asynchronous on the
-// caller's stream.
+// barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).  No device allocation, no
+// global state: every buffer is caller-owned and every call is asynchronous
+// on the caller's stream, except ph0_barcodes_early (which waits to decide how
+// much of the edge order to sort) and ph0_barcodes_noalloc.
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "ph0_common.cuh"
 
@@ -13,7 +15,9 @@ namespace ph0 {
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
                         uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1);
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
-                             int top_bits = kDefaultTopBits);
+                             int top_bits = kDefaultTopBits, int64_t sorted_edges = -1);
+cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
+                               cudaStream_t s);
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
@@ -72,20 +76,14 @@ cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s, int top_bits =
     Header *h = at<Header>(ws, L.hdr);
     cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
     if (e != cudaSuccess) return e;
-    return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s, top_bits);
+    return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s, top_bits, L.m);
 }
 
-// Steps 4-5 plus the read-out: reduce, order the pivot columns by position,
-// emit the bars.  val/key are either the workspace's ping-pong buffers
-// (sort_h != null selects the one holding the sorted data) or the caller's;
-// a is the caller's per-edge index, or null with cpref the workspace's chunk
-// prefixes of the count-mode scan.
-cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
-                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
-                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
-                            ph0_bar *bars, cudaStream_t s, cudaEvent_t after_reduce = nullptr) {
-    Header *h = at<Header>(ws, L.hdr);
-    const int64_t m = n_edges(n);
+// Steps 4-5 on the first m sorted edges (m = n(n-1)/2 on the whole path):
+// the pivot claiming.  val is the workspace's ping-pong buffer (sort_h != null
+// selects the one holding the sorted data) or the caller's.
+cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
+                       const uint32_t *val1, const Header *sort_h, cudaStream_t s) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -100,22 +98,26 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
     A.candr = at<uint32_t>(ws, L.candr);
     A.kill_key = at<unsigned long long>(ws, L.kill_key[0]);
     A.kill_val = at<uint32_t>(ws, L.kill_val[0]);
-    A.h = h;
+    A.h = at<Header>(ws, L.hdr);
     A.trace = at<uint64_t>(ws, L.trace);
     int64_t w0 = 2 * n > 4096 ? 2 * n : 4096;
     A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
-    cudaError_t e = launch_reduce(A, s);
-    if (e != cudaSuccess) return e;
-    if (after_reduce) {
-        e = cudaEventRecord(after_reduce, s);
-        if (e != cudaSuccess) return e;
-    }
+    return launch_reduce(A, s);
+}
+
+// The read-out after run_reduce: order the n-1 pivot columns by position
+// (their discovery order within a window is not the filtration order) and
+// emit the bars.  key as val; a is the caller's per-edge index, or null with
+// cpref the workspace's chunk prefixes of the count-mode scan.
+cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
+                           const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
+                           const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
+                           ph0_bar *bars, cudaStream_t s) {
+    Header *h = at<Header>(ws, L.hdr);
     const int64_t nb = n - 1;
     if (nb <= 0) return cudaSuccess;
-    // order the n-1 pivot columns by sorted position (their discovery order
-    // within a window is not the filtration order)
     Header *kh = at<Header>(ws, L.aux_hdr);
-    e = cudaMemsetAsync(kh, 0, kHeaderBytes, s);
+    cudaError_t e = cudaMemsetAsync(kh, 0, kHeaderBytes, s);
     if (e != cudaSuccess) return e;
     const int64_t ktiles = (nb + kSortTile - 1) / kSortTile;
     e = launch_sort_init(kh, at<uint64_t>(ws, L.kill_look[0]), ktiles, s);
@@ -130,6 +132,21 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
     return launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
                        reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
                        key0, key1, sort_h, a, cpref, bars, s);
+}
+
+// Steps 4-5 plus the read-out on all m = n(n-1)/2 sorted edges.
+cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
+                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
+                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
+                            ph0_bar *bars, cudaStream_t s, cudaEvent_t after_reduce = nullptr) {
+    const int64_t m = n_edges(n);
+    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s);
+    if (e != cudaSuccess) return e;
+    if (after_reduce) {
+        e = cudaEventRecord(after_reduce, s);
+        if (e != cudaSuccess) return e;
+    }
+    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, s);
 }
 
 }  // namespace
@@ -154,7 +171,7 @@ const char *ph0_strerror(int status) {
     }
 }
 
-int32_t ph0_abi_version(void) { return 1; }
+int32_t ph0_abi_version(void) { return 2; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
     if (check_sizes(n, d, d) != PH0_OK) return 0;
@@ -188,6 +205,130 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                  void *ws, size_t ws_bytes, void *stream) {
     return ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, ws, ws_bytes, stream, nullptr);
+}
+
+int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                       void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_sizes(n, d, ld);
+    if (rc != PH0_OK) return rc;
+    if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    if (ws_bytes < L.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto whole = [&]() {  // the whole path, then its device status
+        const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, ws, ws_bytes, stream, nullptr);
+        return r != PH0_OK ? r : ph0_finish(ws, stream, nullptr);
+    };
+    if (n < 3) return whole();
+    const Tune t(nullptr);
+    const int64_t m = L.m;
+    Header *h = at<Header>(ws, L.hdr);
+    Header *sh = at<Header>(ws, L.aux_hdr);  // header of the segment sorts
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
+    uint64_t *dlook = at<uint64_t>(ws, L.dlook);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref), *bins = at<uint32_t>(ws, L.phist);
+
+    // step 1, then the key histogram (read back: the host picks the rounds)
+    cudaError_t e = begin_call(ws, L, s, t.top_bits);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
+    if (e == cudaSuccess) e = launch_prefix_hist(k0, m, h, bins, s);
+    std::vector<uint32_t> hb(kPrefixBins);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb.data(), bins, sizeof(uint32_t) * kPrefixBins, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    Header h0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h0, h, sizeof(Header), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    if (h0.status != PH0_OK) return h0.status;
+    std::vector<int64_t> below(kPrefixBins + 1, 0);  // edges in the bins before bin i
+    for (int i = 0; i < kPrefixBins; ++i) below[i + 1] = below[i] + hb[i];
+    if (below[kPrefixBins] != m) return whole();  // inconsistent histogram: not expected
+
+    // classes of consecutive bin ranges whose cumulative edge counts reach
+    // these fractions of the edges (the last class takes the rest); one
+    // stable radix pass with the class as digit puts them, class by class,
+    // into buffer 1
+    static const double kFractions[] = {0.02, 0.08, 0.25, 0.45};
+    uint32_t bound[kPrefixClasses + 1];
+    int64_t cstart[kPrefixClasses + 1];
+    int nc = 0;
+    bound[0] = 0;
+    cstart[0] = 0;
+    for (double f : kFractions) {
+        const int64_t target = int64_t(f * double(m));
+        uint32_t bnd = bound[nc] + 1;
+        while (bnd < uint32_t(kPrefixBins) && below[bnd] < target) ++bnd;
+        if (bnd >= uint32_t(kPrefixBins)) break;
+        ++nc;
+        bound[nc] = bnd;
+        cstart[nc] = below[bnd];
+    }
+    ++nc;
+    for (int c = nc; c <= kPrefixClasses; ++c) {
+        bound[c] = kPrefixBins;
+        cstart[c] = m;
+    }
+    e = cudaMemsetAsync(sh, 0, kHeaderBytes, s);
+    if (e == cudaSuccess) e = launch_sort_init(sh, look0, L.tiles, s, t.top_bits);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        const uint64_t pk = h0.kmin;
+        const int32_t ps = prefix_shift(h0.kmin, h0.kmax), pn = nc;
+        uint32_t counts[kPrefixClasses];
+        for (int c = 0; c < kPrefixClasses; ++c) counts[c] = uint32_t(c < nc ? cstart[c + 1] - cstart[c] : 0);
+        e = cudaMemcpy(&sh->part_kmin, &pk, sizeof(pk), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(&sh->part_shift, &ps, sizeof(ps), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(&sh->part_nc, &pn, sizeof(pn), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(sh->part_bound, bound, sizeof(bound), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(&sh->hist[0][0], counts, sizeof(counts), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = prepare_sort_kernels();
+    if (e == cudaSuccess) e = launch_sort_pass(k0, k1, v0, v1, m, kClassSlot, look0, look1, sh, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int32_t pst = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&pst, &sh->status, sizeof(pst), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    if (pst != PH0_OK) return pst;
+
+    // rounds: sort the next class in place in buffer 1 (buffer 0, no longer
+    // needed, is the scratch), then run the reduction on the sorted prefix
+    int64_t P = 0;
+    bool done = false;
+    for (int c = 0; c < nc && !done; ++c) {
+        const int64_t c0 = cstart[c], seg = cstart[c + 1] - c0;
+        if (seg == 0) continue;
+        const int64_t stiles = (seg + kSortTile - 1) / kSortTile;
+        e = cudaMemsetAsync(sh, 0, kHeaderBytes, s);
+        if (e == cudaSuccess) e = launch_sort_init(sh, look0, stiles, s, t.top_bits, seg);
+        if (e == cudaSuccess) e = launch_keystats(k1 + c0, seg, sh, s);
+        if (e == cudaSuccess) e = launch_sort_passes(k1 + c0, k0 + c0, v1 + c0, v0 + c0, seg, look0, look1, sh, s);
+        if (e == cudaSuccess) e = launch_copy_if_odd(k1 + c0, k0 + c0, v1 + c0, v0 + c0, seg, sh, s);
+        if (e != cudaSuccess) return PH0_ECUDA;
+        P = c0 + seg;
+        // steps 4-5 on the prefix; enough once it holds n-1 pivots
+        e = run_reduce(ws, L, n, P, v1, v1, nullptr, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        Header hh;
+        if (e == cudaSuccess) e = cudaMemcpy(&hh, h, sizeof(Header), cudaMemcpyDeviceToHost);
+        int32_t sst = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&sst, &sh->status, sizeof(sst), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return PH0_ECUDA;
+        if (hh.status != PH0_OK) return hh.status;
+        if (sst != PH0_OK) return sst;
+        done = int64_t(hh.npiv) >= n - 1;
+    }
+    if (!done) return PH0_EINTERNAL;  // all edges sorted: the reduction always completes
+
+    // step 3 on the prefix (count mode) and the read-out; then the prefix length
+    e = launch_dedupe(k1, k1, nullptr, P, nullptr, cpref, dlook, h, s);
+    if (e == cudaSuccess) e = order_and_emit(ws, L, n, P, v1, v1, k1, k1, nullptr, nullptr, cpref, bars_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h->sorted_edges, &P, sizeof(P), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    return ph0_finish(ws, stream, nullptr);
 }
 
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
@@ -270,6 +411,7 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
         stats->n_bars = hh.n_bars;
         stats->dist_tiles = int64_t(hh.dist_tiles);
         stats->dist_tiles_int = int64_t(hh.dist_tiles_exact_int);
+        stats->sorted_edges = hh.sorted_edges;
     }
     return hh.status;
 }

@@ -43,6 +43,22 @@ constexpr uint64_t kCountMask = ~kFlagMask;
 // flag alone and its low half its count; an unpublished word is all zero.
 constexpr uint32_t kHiAgg = uint32_t(kFlagAgg >> 32), kHiPrefix = uint32_t(kFlagPrefix >> 32);
 
+// The early-terminating path (k_prefix.cu): bins of its key histogram, and
+// at most kPrefixClasses classes (consecutive bin ranges) in its partition
+// of the edges, which runs as radix slot kClassSlot (digit = class).
+constexpr int kPrefixBinBits = 12;
+constexpr int kPrefixBins = 1 << kPrefixBinBits;
+constexpr int kPrefixClasses = 8;
+constexpr int kClassSlot = 8;
+// Bin of a key: (key - kmin) >> shift, with shift such that the key range
+// [kmin, kmax] spans at most kPrefixBins bins.
+__host__ __device__ __forceinline__ int prefix_shift(uint64_t kmin, uint64_t kmax) {
+    const uint64_t span = kmax > kmin ? kmax - kmin : 0;
+    int bits = 0;
+    for (uint64_t x = span; x; x >>= 1) ++bits;
+    return bits > kPrefixBinBits ? bits - kPrefixBinBits : 0;
+}
+
 // --------------------------------------------------------------- header ---
 // Lives at offset 0 of the workspace.  Every counter the kernels share.
 struct Header {
@@ -67,7 +83,14 @@ struct Header {
     uint32_t npiv;               // pivots claimed so far
     uint32_t nlist[2];           // candidate list lengths (ping-pong)
     int32_t top_bits;            // width of a single top radix pass (8 or 9)
-    uint32_t pad[5];
+    uint32_t pad[3];
+    int64_t sorted_edges;        // edges sorted: m, or the prefix of the early path
+    // class partition of the early path (radix slot kClassSlot): the key
+    // bins of its histogram and the classes' bin ranges [bound[c], bound[c+1])
+    uint64_t part_kmin;
+    int32_t part_shift;
+    int32_t part_nc;
+    uint32_t part_bound[kPrefixClasses + 1];
     uint32_t hist[kMaxPasses][kMaxRadix];  // digit histogram per radix pass
 };
 
@@ -91,7 +114,6 @@ constexpr int kTraceWords = 12;
 constexpr int kTailCap = 2048;
 // Keys per chunk of the de-duplication scan's count mode (one prefix each).
 constexpr int kDedupeChunk = 256;
-
 // Byte offsets of every region of the workspace for a cloud of n points in
 // dimension d.  Everything is caller-owned device memory; nothing is
 // allocated by the library.
@@ -100,6 +122,7 @@ struct Layout {
     size_t hdr, aux_hdr;                 // main header, header of the small sorts
     size_t key[2], val[2], look[2];      // edge records, ping-pong, look-back words
     size_t cpref;                        // de-duplication prefix of every key chunk
+    size_t phist;                        // key histogram of the early-terminating path
     size_t dlook;                        // look-back words of the de-duplication scan
     size_t comp, parent, res, cand[2], candr;
     size_t kill_key[2], kill_val[2], kill_look[2];
@@ -125,6 +148,7 @@ struct Layout {
         val[0] = take(4 * size_t(m));
         val[1] = take(4 * size_t(m));
         cpref = take(4 * size_t((m + kDedupeChunk - 1) / kDedupeChunk + 1));
+        phist = take(4 * size_t(kPrefixBins));
         look[0] = take(8 * size_t(tiles) * kMaxRadix);
         look[1] = take(8 * size_t(tiles) * kMaxRadix);
         dlook = take(8 * size_t(tiles + 1));

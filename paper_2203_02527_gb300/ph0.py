@@ -120,6 +120,18 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     return Bars(bars, n, st)
 
 
+def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None) -> Bars:
+    """The same bars as barcodes(), sorting only the prefix of the edge order
+    the reduction needs (ph0_barcodes_early; waits for the GPU).  The stats
+    report the prefix length as sorted_edges."""
+    pts, n, d, ld = _points(pts)
+    ws = ws or _workspace(n, d, pts.device)
+    bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
+    check(_lib.load().ph0_barcodes_early(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, _stream()),
+          "ph0_barcodes_early")
+    return Bars(bars, n, finish(ws))
+
+
 def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None,
                       tuning=None):
     """ph0_barcodes with CUDA events between the stages (waits for the stream).
