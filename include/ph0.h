@@ -220,8 +220,8 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
  * caller workspace it uses a 16 MiB array in the library's device memory
  * (every GPU that loads the library holds it until the process exits); the
  * caller still passes the points and the bars buffer.  Clouds whose workspace
- * would exceed 16 MiB (ph0_workspace_bytes(n, d) > 16 MiB: n above 935 at
- * d = 3, above 929 at d = 32) are rejected with PH0_ETOOBIG before any work is queued.  It
+ * would exceed 16 MiB (ph0_workspace_bytes(n, d) > 16 MiB: n above 934 at
+ * d = 3, above 928 at d = 32) are rejected with PH0_ETOOBIG before any work is queued.  It
  * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
  *
  * The first call on a device looks up the device address of the array for
