@@ -153,6 +153,8 @@ typedef struct {
     float dedupe_ms;         /* step 3                                        */
     float reduce_ms;         /* steps 4-5: pivot claiming                     */
     float emit_ms;           /* ordering of the pivot columns and bar output  */
+    float fixup_ms;          /* step 2: the sort's fix-up of the groups its
+                                passes leave (and the fallback, if taken)   */
 } ph0_profile;
 
 /* ph0_barcodes() with a CUDA event between stages; waits for the stream and

@@ -68,7 +68,7 @@ class Profile(ctypes.Structure):
     _fields_ = [
         ("total_ms", ctypes.c_float), ("dist_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
         ("pass_ms", ctypes.c_float * 8), ("dedupe_ms", ctypes.c_float),
-        ("reduce_ms", ctypes.c_float), ("emit_ms", ctypes.c_float),
+        ("reduce_ms", ctypes.c_float), ("emit_ms", ctypes.c_float), ("fixup_ms", ctypes.c_float),
     ]
 
     def as_dict(self):

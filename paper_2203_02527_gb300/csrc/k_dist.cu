@@ -63,7 +63,9 @@ __device__ __forceinline__ void tile_coords(int64_t lin, int64_t T, int64_t &bi,
 
 __global__ void __launch_bounds__(kDistThreads)
 k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16,
-       uint64_t *__restrict__ key, uint32_t *__restrict__ val, Header *__restrict__ h) {
+       uint64_t *__restrict__ key, uint32_t *__restrict__ val, Header *__restrict__ h,
+       const int32_t *gate) {
+    if (gate && ld_volatile(gate) == 0) return;  // a gated run (the sort's fallback) that is not needed
     // [d][bt] u block, then [d][bt] v block: binary64 values, or int64 fixed
     // point in units of 2^g[k] on the integer path; then g[d], lo[d], hi[d]
     extern __shared__ double s_coord[];
@@ -204,7 +206,8 @@ int dist_tile(int d, int want) {
 }
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
-                        uint32_t *val, Header *h, cudaStream_t s, int split16, int tile) {
+                        uint32_t *val, Header *h, cudaStream_t s, int split16, int tile,
+                        const int32_t *gate) {
     if (n < 2) return cudaSuccess;
     const int bt = dist_tile(d, tile);
     const size_t smem = dist_smem(bt, d);
@@ -216,7 +219,7 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
     const int64_t tiles = T * (T + 1) / 2;
     const int hw16 = (split16 >= 0 && split16 <= 16) ? split16 : kDefaultDistSplit16;
     k_dist<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, hw16, key,
-                                                       val, h);
+                                                       val, h, gate);
     return cudaGetLastError();
 }
 

@@ -58,9 +58,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp
 
 // Header fields a sort needs zeroed: histograms, key range, tile counters.
 __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int top_bits,
-                            int64_t sorted_edges) {
+                            int64_t sorted_edges, const int32_t *gate) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    if (gate && ld_volatile(gate) == 0) look_words = 0;  // a gated sort that will not run
     if (tid == 0) {
         if (sorted_edges >= 0) h->sorted_edges = sorted_edges;
         h->kmin = ~0ull;
@@ -537,6 +538,118 @@ __global__ void k_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *
     }
 }
 
+// ---- the short sort: the passes over key bits 16 and up, then a fix-up ----
+//
+// The passes from slot kShortFirstSlot on (bytes 2..5 and the top part) sort
+// the records by key >> kShortShift; as every pass is stable, each group of
+// equal key >> kShortShift is still in input order, i.e. in increasing value
+// (u << 16 | v).  The fix-up then sorts every group by the whole key, stably,
+// which completes the sort.  Groups of two or more records are rare (their
+// keys agree in all but the low 16 bits), so the fix-up is a streaming check
+// of neighbours; a group of at most kFixCap records is sorted by the thread
+// at its start, and an out-of-order group above kFixCap (only clouds whose
+// distances crowd into tiny ranges) sets h->fixup_fallback, on which the
+// caller gates a complete sort.  The first short slot is even, so the records
+// end where a complete sort leaves them: buffer (passes & 1).
+constexpr int kShortFirstSlot = 2;
+constexpr int kShortShift = kRadixBits * kShortFirstSlot;
+constexpr int kFixCap = 32;
+
+// The check of one record at p (its key kp, the previous kq and next kn;
+// ~0 beyond the ends): a group start sorts its group when it holds 2..kFixCap
+// records out of order; an inversion inside a longer group reports it.
+__device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
+                                         uint64_t kq, uint64_t kn, bool &long_unsorted) {
+    // group ids never change here (the fix-up permutes within groups), so
+    // reads that race with a fix-up see the same ids
+    const uint64_t g = kp >> kShortShift;
+    if ((kq >> kShortShift) != g || p == 0) {
+        if ((kn >> kShortShift) != g) return;  // a group of one
+        int sz = 2;  // a group starts here: its size, up to kFixCap + 1
+        while (sz <= kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
+        if (sz > kFixCap) return;  // long: its inversions are checked at their own positions
+        uint64_t kk[kFixCap];
+        uint32_t vv[kFixCap];
+        bool sorted = true;
+        for (int i = 0; i < sz; ++i) {
+            kk[i] = keys[p + i];
+            vv[i] = vals[p + i];
+            if (i > 0 && kk[i] < kk[i - 1]) sorted = false;
+        }
+        if (sorted) return;
+        for (int i = 1; i < sz; ++i) {  // stable: an equal key stays behind
+            const uint64_t k = kk[i];
+            const uint32_t v = vv[i];
+            int j = i - 1;
+            while (j >= 0 && kk[j] > k) {
+                kk[j + 1] = kk[j];
+                vv[j + 1] = vv[j];
+                --j;
+            }
+            kk[j + 1] = k;
+            vv[j + 1] = v;
+        }
+        for (int i = 0; i < sz; ++i) {
+            keys[p + i] = kk[i];
+            vals[p + i] = vv[i];
+        }
+    } else if (kp < kq) {
+        // an inversion: fine inside a group of at most kFixCap (its first
+        // thread sorts it), else the group is out of order
+        int64_t st = -1;
+        for (int i = 1; i <= kFixCap; ++i)
+            if (p - i < 0 || (keys[p - i] >> kShortShift) != g) {
+                st = p - i + 1;
+                break;
+            }
+        if (st < 0 || (st + kFixCap < m && (keys[st + kFixCap] >> kShortShift) == g)) long_unsorted = true;
+    }
+}
+
+// Each thread takes kFixPer consecutive records (vector loads; a warp covers
+// 32 x kFixPer records at a time); neighbours come from its own registers,
+// from a shuffle at its ends, or from a single load at the warp's ends.
+constexpr int kFixPer = 8;
+__global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
+                                                     uint32_t *vals1, int64_t m, Header *h) {
+    const Plan plan = make_plan(h);
+    uint64_t *keys = (plan.passes & 1) ? keys1 : keys0;
+    uint32_t *vals = (plan.passes & 1) ? vals1 : vals0;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    constexpr int64_t kChunk = 32 * kFixPer;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    bool long_unsorted = false;
+    for (int64_t b = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kChunk; b < m; b += nw * kChunk) {
+        const int64_t p0 = b + int64_t(lane) * kFixPer;
+        uint64_t k[kFixPer];
+        if (vec && p0 + kFixPer <= m) {
+            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(keys + p0);
+#pragma unroll
+            for (int i = 0; i < kFixPer / 2; ++i) {
+                const ulonglong2 w = src[i];
+                k[2 * i] = w.x;
+                k[2 * i + 1] = w.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kFixPer; ++i) k[i] = p0 + i < m ? keys[p0 + i] : ~0ull;  // ~0: no key
+        }
+        uint64_t prev = __shfl_up_sync(0xffffffffu, k[kFixPer - 1], 1);
+        uint64_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] : ~0ull;
+        if (lane == 31) next = b + kChunk < m ? keys[b + kChunk] : ~0ull;
+#pragma unroll
+        for (int i = 0; i < kFixPer; ++i) {
+            const int64_t p = p0 + i;
+            if (p < m)
+                fixup_at(keys, vals, m, p, k[i], i > 0 ? k[i - 1] : prev, i + 1 < kFixPer ? k[i + 1] : next,
+                         long_unsorted);
+        }
+    }
+    if (long_unsorted) atomicExch(&h->fixup_fallback, 1);
+}
+
 // ------------------------------------------------------------------ host ---
 template <int RADIX>
 constexpr size_t sort_smem() { return sizeof(SortSmem<RADIX>); }
@@ -550,12 +663,12 @@ int sm_count() {
 
 // Zero the sort's counters and first look-back buffer (sized for 512 buckets).
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s, int top_bits,
-                             int64_t sorted_edges) {
+                             int64_t sorted_edges, const int32_t *gate) {
     const int64_t words = tiles * kMaxRadix;
     int blocks = int((words + 255) / 256);
     if (blocks < 8) blocks = 8;
     if (blocks > 4 * sm_count() * 8) blocks = 4 * sm_count() * 8;
-    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words, top_bits == 8 ? 8 : 9, sorted_edges);
+    k_sort_init<<<blocks, 256, 0, s>>>(h, look0, words, top_bits == 8 ? 8 : 9, sorted_edges, gate);
     return cudaGetLastError();
 }
 
@@ -637,6 +750,34 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The short sort of the records in buffer 0 (see k_sort_fixup): the passes
+// from slot kShortFirstSlot on, then the fix-up.  look0 must be zeroed
+// (launch_sort_init), h's histograms complete.  The records end sorted in
+// buffer (passes & 1), unless h->fixup_fallback.
+cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
+                              Header *h, cudaStream_t s);
+cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    cudaError_t e = prepare_sort_kernels();
+    if (e != cudaSuccess) return e;
+    for (int p = kShortFirstSlot; p < kMaxPasses; ++p) {
+        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_sort_fixup(keys0, keys1, vals0, vals1, m, h, s);
+}
+
+cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
+                              Header *h, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    int64_t blocks = (m + 255) / 256;
+    const int64_t cap = int64_t(sm_count()) * 8;
+    if (blocks > cap) blocks = cap;
+    k_sort_fixup<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,

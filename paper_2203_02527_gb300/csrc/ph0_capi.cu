@@ -13,9 +13,16 @@
 namespace ph0 {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
-                        uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1);
+                        uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1,
+                        const int32_t *gate = nullptr);
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
-                             int top_bits = kDefaultTopBits, int64_t sorted_edges = -1);
+                             int top_bits = kDefaultTopBits, int64_t sorted_edges = -1,
+                             const int32_t *gate = nullptr);
+cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s);
+cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
+                              Header *h, cudaStream_t s);
+constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
                                cudaStream_t s);
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
@@ -77,6 +84,41 @@ cudaError_t begin_call(void *ws, const Layout &L, cudaStream_t s, int top_bits =
     cudaError_t e = cudaMemsetAsync(h, 0, kHeaderBytes, s);
     if (e != cudaSuccess) return e;
     return launch_sort_init(h, at<uint64_t>(ws, L.look[0]), L.tiles, s, top_bits, L.m);
+}
+
+// The gated fallback of the whole path's sort: when the short sort's fix-up
+// met a long group out of order (h->fixup_fallback), step 1 again and the
+// complete sort, in the auxiliary header; otherwise every kernel returns at
+// once (the distance kernel reads the gate, the radix passes a key range that
+// was never set).  Both sorts leave the records in buffer (passes & 1) of the
+// same plan (the keys, hence the key range, are the same).
+cudaError_t sort_fallback(void *ws, const Layout &L, const float *pts, int64_t n, int32_t d, int64_t ld,
+                          const Tune &t, cudaStream_t s) {
+    Header *h = at<Header>(ws, L.hdr), *fh = at<Header>(ws, L.aux_hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
+    const int32_t *gate = &h->fixup_fallback;
+    cudaError_t e = cudaMemsetAsync(fh, 0, kHeaderBytes, s);
+    if (e == cudaSuccess) e = launch_sort_init(fh, look0, L.tiles, s, t.top_bits, -1, gate);
+    if (e == cudaSuccess) e = launch_dist(pts, n, d, ld, k0, v0, fh, s, t.split16, t.tile, gate);
+    if (e == cudaSuccess) e = launch_sort_passes(k0, k1, v0, v1, L.m, look0, look1, fh, s);
+    return e;
+}
+
+// Step 2 of the whole path (the records of step 1 in buffer 0, h's
+// histograms complete): the short sort (the passes over key bits 16 and up,
+// then a fix-up of the groups they leave; k_sort.cu) and its gated
+// fallback.  The sorted records end in buffer (passes & 1) of h's plan.
+cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, int32_t d, int64_t ld,
+                       const Tune &t, cudaStream_t s) {
+    if (L.m <= 0) return cudaSuccess;
+    cudaError_t e = launch_sort_short(at<uint64_t>(ws, L.key[0]), at<uint64_t>(ws, L.key[1]),
+                                      at<uint32_t>(ws, L.val[0]), at<uint32_t>(ws, L.val[1]), L.m,
+                                      at<uint64_t>(ws, L.look[0]), at<uint64_t>(ws, L.look[1]),
+                                      at<Header>(ws, L.hdr), s);
+    if (e != cudaSuccess) return e;
+    return sort_fallback(ws, L, pts, n, d, ld, t, s);
 }
 
 // Steps 4-5 on the first m sorted edges (m = n(n-1)/2 on the whole path):
@@ -194,9 +236,7 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
-    if (e == cudaSuccess)
-        e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
-                               at<uint64_t>(ws, L.look[1]), h, s);
+    if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     return cuda_status(e);
@@ -355,8 +395,10 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
         for (int i = 0; i < made - 1; ++i) cudaEventDestroy(ev[i]);
         return PH0_ECUDA;
     }
-    // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | dedupe | ev[2+P] | reduce | ev[3+P] |
-    // order pivots, emit | ev[4+P]   (P = kMaxPasses launches; unneeded passes return at once)
+    // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | fix-up, gated fallback | ev[2+P] |
+    // dedupe | ev[3+P] | reduce | ev[4+P] | order pivots, emit | ev[5+P]
+    // (P = kMaxPasses; the short sort launches the passes from slot 3 on,
+    // with the buffers swapped; passes that are not needed return at once)
     const Tune t(tuning);
     e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
@@ -364,14 +406,17 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
-        if (L.m > 0) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
+        if (L.m > 0 && p >= kShortSortFirstSlot) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
     }
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, s);
+    if (e == cudaSuccess && L.m > 0) e = sort_fallback(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s, ev[3 + kMaxPasses]);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4 + kMaxPasses], s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4 + kMaxPasses]);
+    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 + kMaxPasses], s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s, ev[4 + kMaxPasses]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5 + kMaxPasses], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[5 + kMaxPasses]);
     if (e == cudaSuccess) {
         auto span = [&](int i, int j) {
             float ms = 0.f;
@@ -379,13 +424,14 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
             return ms;
         };
         std::memset(prof, 0, sizeof(*prof));
-        prof->total_ms = span(0, 4 + kMaxPasses);
+        prof->total_ms = span(0, 5 + kMaxPasses);
         prof->dist_ms = span(0, 1);
         for (int p = 0; p < kMaxPasses; ++p) prof->pass_ms[p] = span(1 + p, 2 + p);
-        prof->sort_ms = span(1, 1 + kMaxPasses);
-        prof->dedupe_ms = span(1 + kMaxPasses, 2 + kMaxPasses);
-        prof->reduce_ms = span(2 + kMaxPasses, 3 + kMaxPasses);
-        prof->emit_ms = span(3 + kMaxPasses, 4 + kMaxPasses);
+        prof->fixup_ms = span(1 + kMaxPasses, 2 + kMaxPasses);
+        prof->sort_ms = span(1, 2 + kMaxPasses);
+        prof->dedupe_ms = span(2 + kMaxPasses, 3 + kMaxPasses);
+        prof->reduce_ms = span(3 + kMaxPasses, 4 + kMaxPasses);
+        prof->emit_ms = span(4 + kMaxPasses, 5 + kMaxPasses);
     }
     for (int i = 0; i < kEv; ++i) cudaEventDestroy(ev[i]);
     return cuda_status(e);
@@ -573,11 +619,10 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     // the array keeps the previous call's contents: begin_call zeroes the
     // header and the first look-back buffer, and every later stage clears or
     // overwrites what it reads before reading it
+    const Tune t(nullptr);
     cudaError_t e = begin_call(ws, L, s);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
-    if (e == cudaSuccess)
-        e = launch_sort_passes(k0, k1, v0, v1, L.m, at<uint64_t>(ws, L.look[0]),
-                               at<uint64_t>(ws, L.look[1]), h, s);
+    if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

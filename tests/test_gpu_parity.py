@@ -171,6 +171,29 @@ def test_step_oracle_pins_hold_on_gpu_output():
     assert pins.check_bars_sweep(x[:12], ph0.barcodes(_cuda(x[:12])).numpy()) is None
 
 
+def test_crowded_distances_take_the_complete_sort():
+    """Simplex vertices with off-diagonal perturbations of ~1e-12: all 190
+    squared distances (189 distinct) lie within 2^-36 below 2, so the sort's
+    passes over key bits 16 and up leave one long group out of order, and
+    the fix-up hands over to the complete sort (the same bars)."""
+    ph0 = _ph0()
+    rng = np.random.default_rng(12)
+    x = np.eye(20, dtype=np.float32)
+    off = (rng.random((20, 20)) * 1e-12).astype(np.float32)
+    np.fill_diagonal(off, 0)
+    x = (x + off).astype(np.float32)
+    assert np.all(np.diag(x) == 1)
+    want = oracle.barcodes(x)[0]
+    assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), want)
+    d2 = want["death_sq"]
+    assert d2.min() < 2 and d2.max() - d2.min() < 2.0 ** -36
+    # and the plain step sequence agrees
+    ref = oracle.pipeline(x)
+    key, val = ph0.distances(_cuda(x))
+    ph0.sort_pairs(key, val)
+    np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
+
+
 @pytest.mark.parametrize("split,tile,top", [(0, 128, 9), (5, 64, 9), (16, 32, 8), (11, 128, 8)])
 def test_tuning_changes_no_bit(split, tile, top):
     """Every tuning (distance split, tile size, top radix width) gives the
