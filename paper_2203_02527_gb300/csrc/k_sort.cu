@@ -555,19 +555,20 @@ constexpr int kShortFirstSlot = 2;
 constexpr int kShortShift = kRadixBits * kShortFirstSlot;
 constexpr int kFixCap = 32;
 
-// The check of one record at p (its key kp, the previous kq and next kn;
-// ~0 beyond the ends): a group start sorts its group when it holds 2..kFixCap
-// records out of order; an inversion inside a longer group reports it.
-__device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
-                                         uint64_t kq, uint64_t kn, bool &long_unsorted) {
+// The rare cases of the check of one record at p (see fixup_at), kept out
+// of line so that the streaming loop stays small: a group start of a group
+// of two or more records sorts its group when it holds 2..kFixCap records out
+// of order; an inversion inside a longer group reports it.  Returns whether
+// a long group is out of order.
+__device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
+                                        uint64_t kq, bool start) {
     // group ids never change here (the fix-up permutes within groups), so
     // reads that race with a fix-up see the same ids
     const uint64_t g = kp >> kShortShift;
-    if ((kq >> kShortShift) != g || p == 0) {
-        if ((kn >> kShortShift) != g) return;  // a group of one
+    if (start) {
         int sz = 2;  // a group starts here: its size, up to kFixCap + 1
         while (sz <= kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
-        if (sz > kFixCap) return;  // long: its inversions are checked at their own positions
+        if (sz > kFixCap) return false;  // long: its inversions are checked at their own positions
         uint64_t kk[kFixCap];
         uint32_t vv[kFixCap];
         bool sorted = true;
@@ -576,7 +577,7 @@ __device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t
             vv[i] = vals[p + i];
             if (i > 0 && kk[i] < kk[i - 1]) sorted = false;
         }
-        if (sorted) return;
+        if (sorted) return false;
         for (int i = 1; i < sz; ++i) {  // stable: an equal key stays behind
             const uint64_t k = kk[i];
             const uint32_t v = vv[i];
@@ -593,17 +594,28 @@ __device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t
             keys[p + i] = kk[i];
             vals[p + i] = vv[i];
         }
-    } else if (kp < kq) {
-        // an inversion: fine inside a group of at most kFixCap (its first
-        // thread sorts it), else the group is out of order
-        int64_t st = -1;
-        for (int i = 1; i <= kFixCap; ++i)
-            if (p - i < 0 || (keys[p - i] >> kShortShift) != g) {
-                st = p - i + 1;
-                break;
-            }
-        if (st < 0 || (st + kFixCap < m && (keys[st + kFixCap] >> kShortShift) == g)) long_unsorted = true;
+        return false;
     }
+    // an inversion: fine inside a group of at most kFixCap (its first thread
+    // sorts it), else the group is out of order
+    int64_t st = -1;
+    for (int i = 1; i <= kFixCap; ++i)
+        if (p - i < 0 || (keys[p - i] >> kShortShift) != g) {
+            st = p - i + 1;
+            break;
+        }
+    return st < 0 || (st + kFixCap < m && (keys[st + kFixCap] >> kShortShift) == g);
+}
+
+// The check of one record at p (its key kp, the previous kq and next kn;
+// ~0 beyond the ends): nothing to do unless p starts a group of two or more
+// records or is an inversion.
+__device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
+                                         uint64_t kq, uint64_t kn, bool &long_unsorted) {
+    const uint64_t g = kp >> kShortShift;
+    const bool start = (kq >> kShortShift) != g || p == 0;
+    if (start ? (kn >> kShortShift) == g : kp < kq)
+        long_unsorted |= fixup_rare(keys, vals, m, p, kp, kq, start);
 }
 
 // Each thread takes kFixPer consecutive records (vector loads; a warp covers

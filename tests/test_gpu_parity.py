@@ -171,6 +171,24 @@ def test_step_oracle_pins_hold_on_gpu_output():
     assert pins.check_bars_sweep(x[:12], ph0.barcodes(_cuda(x[:12])).numpy()) is None
 
 
+def test_short_sort_fixes_groups_in_place():
+    """Simplex vertices (n=24) with off-diagonal perturbations of ~1e-10: the
+    276 squared distances fall into 27 groups of equal key >> 16 holding up to
+    25 records, 129 of them out of order; the fix-up sorts every group in
+    place (no group is long enough for the complete sort)."""
+    ph0 = _ph0()
+    rng = np.random.default_rng(13)
+    x = np.eye(24, dtype=np.float32)
+    off = (rng.random((24, 24)) * 1e-10).astype(np.float32)
+    np.fill_diagonal(off, 0)
+    x = (x + off).astype(np.float32)
+    ref = oracle.pipeline(x)
+    keys = ref["d2"].view(np.uint64)
+    groups, counts = np.unique(keys >> np.uint64(16), return_counts=True)
+    assert 2 <= counts.max() <= 32 and len(groups) < len(keys) // 4
+    assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), ref["bars"])
+
+
 def test_crowded_distances_take_the_complete_sort():
     """Simplex vertices with off-diagonal perturbations of ~1e-12: all 190
     squared distances (189 distinct) lie within 2^-36 below 2, so the sort's
