@@ -230,7 +230,7 @@ def run_ours(args, rank, world, local_rank):
     # the prefix of the edge order that the reduction needs
     early_ms = []
     early_same = True
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.no_early else args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -239,10 +239,12 @@ def run_ours(args, rank, world, local_rank):
         early_same = early_same and bool(torch.equal(eb.raw, bars))
         if i >= args.warmup:
             early_ms.append((t1 - t0) * 1e3)
-    early_t = max_over_ranks(float(np.mean(early_ms)), dev)
-    early = {"value": job_throughput(m, world, early_t), "unit": "edges/s", "ms_per_step": early_t,
-             "sorted_edges": int(eb.stats["sorted_edges"]), "identical_to_whole_path": early_same,
-             "timing": "host clock around the synchronous call, L2 flushed before each"}
+    early = None
+    if early_ms:
+        early_t = max_over_ranks(float(np.mean(early_ms)), dev)
+        early = {"value": job_throughput(m, world, early_t), "unit": "edges/s", "ms_per_step": early_t,
+                 "sorted_edges": int(eb.stats["sorted_edges"]), "identical_to_whole_path": early_same,
+                 "timing": "host clock around the synchronous call, L2 flushed before each"}
 
     if rank != 0:
         return
@@ -381,6 +383,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
+    ap.add_argument("--no-early", action="store_true", help="skip timing the early-terminating path")
     ap.add_argument("--serve-clouds", type=int, default=10000,
                     help="clouds in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-budget", type=int, default=64, help="serving device arena, GiB")
