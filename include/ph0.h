@@ -178,9 +178,9 @@ int ph0_trace_windows(const void *ws, int64_t n, int32_t d, void *stream, uint64
 
 /* ---- step entry points (each one step of the path, for testing and reuse) ---- */
 
-/* Step 1 (Sec. 2 "calculate the distance between every pair of points";
- * Sec. 4 step 1).  Writes, for every edge u<v at index
- * e = u*(2n-u-1)/2 + (v-u-1) (lexicographic order):
+/* Step 1 (Sec. 2: the distance of every pair of points; Sec. 4 step 1).
+ * Writes, for every edge u<v at index e = u*(2n-u-1)/2 + (v-u-1)
+ * (lexicographic order):
  *   key_dev[e] = bit pattern of the binary64 squared distance (uint64),
  *   val_dev[e] = (u << 16) | v.
  * key_dev: uint64 [E], val_dev: uint32 [E], E = n(n-1)/2, 16-byte aligned. */
@@ -188,7 +188,7 @@ int ph0_distances(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                   uint64_t *key_dev, uint32_t *val_dev,
                   void *ws, size_t ws_bytes, void *stream);
 
-/* Step 2 (Sec. 2 "sort it in increasing order"; Sec. 4 step 2).  Stable sort
+/* Step 2 (Sec. 2: the distances in increasing order; Sec. 4 step 2).  Stable sort
  * of the m (key, val) pairs by key, in place; keys are binary64 bit patterns
  * of non-negative numbers (unsigned order = numeric order).  Input in val
  * order gives the total order (distance, u, v).  m <= 2^31 - 1; `ws` must be
@@ -196,13 +196,13 @@ int ph0_distances(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
 int ph0_sort(uint64_t *key_dev, uint32_t *val_dev, int64_t m,
              void *ws, size_t ws_bytes, void *stream);
 
-/* Step 3 (Sec. 2 "Remove duplicate elements in E and call it D ... a is the
- * index of edge j in D which ranges from 1 to the length of D").
+/* Step 3 (Sec. 2: D is the sorted distances without repeats, and a(j) is the
+ * position, from 1 to |D|, of edge j's distance in D).
  *   key_sorted_dev  uint64 [m] sorted keys;  a_dev  uint32 [m] output. */
 int ph0_dedupe(const uint64_t *key_sorted_dev, int64_t m, uint32_t *a_dev,
                void *ws, size_t ws_bytes, void *stream);
 
-/* Steps 4-5 (Sec. 2 "build a matrix M ... column reduce this matrix"; Sec. 4
+/* Steps 4-5 (Sec. 2: the matrix M of the edges and its column reduction; Sec. 4
  * steps 3-5).  Column p of M has the rows u_p, v_p of val_sorted_dev[p], both
  * t^a[p]; it is never materialised.  The columns are reduced in order with a
  * pivot table claimed by atomic priority (lower filtration position wins,

@@ -45,8 +45,8 @@
 #define ERR_STATE -3
 
 /* --------------------------------------------------------------------------
- * Step 1: distances (Sec. 2 "calculate the distance between every pair of
- * points"; Sec. 4 step 1).  Edge e enumerates pairs u<v lexicographically:
+ * Step 1: distances (Sec. 2: the distance of every pair of points; Sec. 4
+ * step 1).  Edge e enumerates pairs u<v lexicographically:
  * (0,1),(0,2),...,(0,N-1),(1,2),...  The output is the squared distance;
  * the distance itself is its square root, a monotone map, so sorting and
  * de-duplicating squared distances orders and merges the distances alike.
@@ -130,7 +130,7 @@ int ph0o_sort_edges(const double *d2, const int32_t *u, const int32_t *v,
 }
 
 /* --------------------------------------------------------------------------
- * Step 3: "Remove duplicate elements in E and call it D" (Sec. 2); a(j) is
+ * Step 3: D is E without repeated distances (Sec. 2); a(j) is
  * the index, from 1, of edge j's distance in D.  Input: distances already
  * sorted.  Output: a per sorted position, and |D|.
  * ------------------------------------------------------------------------ */

@@ -1,6 +1,6 @@
 // k_dist.cu -- step 1 of the barcode path: all pairwise squared distances
-// (Rawson, Sec. 2 "calculate the distance between every pair of points";
-// Sec. 3 notes the factor-2 saving from symmetry; Sec. 4 step 1).
+// (Rawson, Sec. 2: the distance of every pair of points; Sec. 3 notes the
+// factor-2 saving from symmetry; Sec. 4 step 1).
 //
 // One CTA per tile of the upper triangle: a block of BT row points (u) by a
 // block of BT column points (v), v-block >= u-block.  The binary32

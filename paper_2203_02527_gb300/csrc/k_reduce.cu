@@ -10,8 +10,8 @@
 // vertex form a tree whose root is the smallest vertex of its connected
 // component, and reducing column p = {u, v} ends either in zero (u and v are
 // already connected by earlier columns: no bar) or with the pivot
-// L = max(root(u), root(v)) claimed by p: a bar (0, a(p)) (Sec. 2, "the
-// remaining nonzero diagonal entries t^b correspond to the barcode (0,b)").
+// L = max(root(u), root(v)) claimed by p: a bar (0, a(p)) (Sec. 2: each
+// pivot entry t^b left after the reduction gives the bar (0, b)).
 // This is the pairing the left-to-right reduction produces, so the kernel
 // keeps, per vertex, the root of its component (a flattened pivot table) and
 // never stores M.

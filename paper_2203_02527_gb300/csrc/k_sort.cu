@@ -1,6 +1,6 @@
 // k_sort.cu -- step 2 of the barcode path: sort the edges by distance
-// (Rawson, Sec. 2 "sort it in increasing order"; Sec. 4 step 2; the paper
-// used a library sort, Sec. 4.1).
+// (Rawson, Sec. 2: the distances in increasing order; Sec. 4 step 2; the
+// paper used a library sort, Sec. 4.1).
 //
 // A stable least-significant-digit radix sort of (key = binary64 bit pattern
 // of the squared distance, val = (u << 16) | v) pairs.  The keys are
@@ -17,11 +17,17 @@
 // earlier tiles by decoupled look-back over per-tile status words.  Ranking
 // finds the lanes of a warp that share a digit by intersecting one warp
 // ballot per digit bit (8-bit digits) or by one warp match (the 9-bit top
-// digit, which is concentrated on few values).  The tile is reordered by digit in shared memory and
-// written out as contiguous runs, one run per digit.  The six low-digit
-// histograms come from the distance kernel; the last low pass histograms the
-// top digit(s) while it writes, so no pass needs an extra read of the keys.
-// Every wait is bounded.
+// digit, which is concentrated on few values).  The tile is reordered by
+// digit in shared memory and written out as contiguous runs, one run per
+// digit.  The six low-digit histograms come from the distance kernel; the
+// last low pass histograms the top digit(s) while it writes, so no pass
+// needs an extra read of the keys.  Every wait is bounded.
+//
+// The whole path sorts with the short sort (launch_sort_short): the passes
+// from slot 2 on, then a fix-up of the rare groups of records whose keys
+// agree above bit 16 (k_sort_fixup).  The step entry point and the early
+// path run every pass.  The early path's partition into distance classes is
+// one more pass (slot kClassSlot, digit = class).
 #include "ph0_common.cuh"
 
 namespace ph0 {
