@@ -149,7 +149,8 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
 // above), one warp per chunk, grid-stride.
 __global__ void __launch_bounds__(256)
 k_chunk_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
-              uint32_t *__restrict__ cnt) {
+              uint32_t *__restrict__ cnt, const int32_t *gate) {
+    if (gate && ld_volatile(gate) == 0) return;  // counts already made (by the sort's fix-up)
     constexpr int kPer = kDedupeChunk / 32;
     const uint64_t *keys = keys0;
     if (sort_h) keys = (make_plan(sort_h).passes & 1) ? keys1 : keys0;
@@ -269,6 +270,10 @@ k_chunk_scan(uint32_t *__restrict__ cnt, int64_t chunks, uint64_t *look, Header 
     }
 }
 
+cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
+                                uint32_t *cnt, const int32_t *gate, cudaStream_t s);
+cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s);
+
 // Per-edge mode (a != null) or count mode (cpref != null, which must hold
 // one word per chunk of kDedupeChunk keys).
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
@@ -282,6 +287,15 @@ cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const He
         k_dedupe<<<unsigned(tiles), kDedupeThreads, 0, s>>>(keys0, keys1, sort_h, m, a, look, h);
         return cudaGetLastError();
     }
+    cudaError_t e = launch_dedupe_count(keys0, keys1, sort_h, m, cpref, nullptr, s);
+    if (e != cudaSuccess) return e;
+    return launch_dedupe_scan(cpref, m, look, h, s);
+}
+
+// Count mode, pass 1 alone (gate: only if *gate != 0).
+cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
+                                uint32_t *cnt, const int32_t *gate, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
     const int64_t chunks = (m + kDedupeChunk - 1) / kDedupeChunk;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -289,11 +303,16 @@ cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const He
     int64_t blocks = (chunks + 7) / 8;  // 8 warps per block
     const int64_t cap = int64_t(sms > 0 ? sms : 1) * 8;
     if (blocks > cap) blocks = cap;
-    k_chunk_count<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, sort_h, m, cpref);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    k_chunk_count<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, sort_h, m, cnt, gate);
+    return cudaGetLastError();
+}
+
+// Count mode, pass 2 alone: the chunk counts in cpref become chunk prefixes.
+cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t chunks = (m + kDedupeChunk - 1) / kDedupeChunk;
     const int64_t stiles = (chunks + kScanTile - 1) / kScanTile;
-    e = cudaMemsetAsync(look, 0, sizeof(uint64_t) * size_t(stiles), s);
+    cudaError_t e = cudaMemsetAsync(look, 0, sizeof(uint64_t) * size_t(stiles), s);
     if (e != cudaSuccess) return e;
     k_chunk_scan<<<unsigned(stiles), kScanThreads, 0, s>>>(cpref, chunks, look, h);
     return cudaGetLastError();

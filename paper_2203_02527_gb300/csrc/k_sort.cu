@@ -561,13 +561,66 @@ constexpr int kShortFirstSlot = 2;
 constexpr int kShortShift = kRadixBits * kShortFirstSlot;
 constexpr int kFixCap = 32;
 
+// The de-duplication flag of every record (a new distance value: p == 0 or
+// key[p] != key[p-1]) is counted per chunk of kDedupeChunk records as the
+// fix-up streams the keys, so step 3 needs no pass of its own; a warp step
+// covers exactly one chunk.  Sorting a group changes the flags inside it:
+// the thread that sorts a group adds the difference to its chunk's count,
+// and a group that would need sorting across the end of its chunk (whose
+// records another warp may be counting meanwhile) is left to a second
+// kernel, which sorts it once every count is written and corrects both
+// chunks' counts.
+// Sorts the group of sz records at p (2 <= sz <= kFixCap) by key, stably;
+// returns the change in the number of new-value flags inside it, and, per
+// record i, that change in dflag[i] when dflag is given.
+__device__ int sort_group(uint64_t *keys, uint32_t *vals, int64_t p, int sz, int8_t *dflag) {
+    uint64_t kk[kFixCap];
+    uint32_t vv[kFixCap];
+    if (dflag)
+        for (int i = 0; i < sz; ++i) dflag[i] = 0;
+    bool sorted = true;
+    for (int i = 0; i < sz; ++i) {
+        kk[i] = keys[p + i];
+        vv[i] = vals[p + i];
+        if (i > 0 && kk[i] < kk[i - 1]) sorted = false;
+    }
+    if (sorted) return 0;
+    int8_t before[kFixCap];
+    for (int i = 1; i < sz; ++i) before[i] = kk[i] != kk[i - 1];
+    for (int i = 1; i < sz; ++i) {  // stable: an equal key stays behind
+        const uint64_t k = kk[i];
+        const uint32_t v = vv[i];
+        int j = i - 1;
+        while (j >= 0 && kk[j] > k) {
+            kk[j + 1] = kk[j];
+            vv[j + 1] = vv[j];
+            --j;
+        }
+        kk[j + 1] = k;
+        vv[j + 1] = v;
+    }
+    int delta = 0;
+    for (int i = 0; i < sz; ++i) {
+        keys[p + i] = kk[i];
+        vals[p + i] = vv[i];
+        if (i > 0) {
+            const int d = int(kk[i] != kk[i - 1]) - before[i];
+            delta += d;
+            if (dflag) dflag[i] = int8_t(d);
+        }
+    }
+    return delta;
+}
+
 // The rare cases of the check of one record at p (see fixup_at), kept out
-// of line so that the streaming loop stays small: a group start of a group
-// of two or more records sorts its group when it holds 2..kFixCap records out
-// of order; an inversion inside a longer group reports it.  Returns whether
-// a long group is out of order.
+// of line so that the streaming loop stays small: the start of a group of
+// two or more records sorts its group (when it holds at most kFixCap
+// records and ends in the chunk; else it defers it), adding the change of
+// its flags to *delta; an inversion inside a longer group reports it.
+// Returns whether a long group is out of order.
 __device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
-                                        uint64_t kq, bool start) {
+                                        bool start, int64_t chunk_end, uint64_t *defer_list,
+                                        uint32_t *defer_count, int *delta) {
     // group ids never change here (the fix-up permutes within groups), so
     // reads that race with a fix-up see the same ids
     const uint64_t g = kp >> kShortShift;
@@ -575,35 +628,15 @@ __device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t 
         int sz = 2;  // a group starts here: its size, up to kFixCap + 1
         while (sz <= kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
         if (sz > kFixCap) return false;  // long: its inversions are checked at their own positions
-        uint64_t kk[kFixCap];
-        uint32_t vv[kFixCap];
-        bool sorted = true;
-        for (int i = 0; i < sz; ++i) {
-            kk[i] = keys[p + i];
-            vv[i] = vals[p + i];
-            if (i > 0 && kk[i] < kk[i - 1]) sorted = false;
+        if (p + sz > chunk_end) {  // reaches into the next chunk: the second kernel sorts it
+            defer_list[atomicAdd(defer_count, 1u)] = uint64_t(p);
+            return false;
         }
-        if (sorted) return false;
-        for (int i = 1; i < sz; ++i) {  // stable: an equal key stays behind
-            const uint64_t k = kk[i];
-            const uint32_t v = vv[i];
-            int j = i - 1;
-            while (j >= 0 && kk[j] > k) {
-                kk[j + 1] = kk[j];
-                vv[j + 1] = vv[j];
-                --j;
-            }
-            kk[j + 1] = k;
-            vv[j + 1] = v;
-        }
-        for (int i = 0; i < sz; ++i) {
-            keys[p + i] = kk[i];
-            vals[p + i] = vv[i];
-        }
+        *delta += sort_group(keys, vals, p, sz, nullptr);
         return false;
     }
-    // an inversion: fine inside a group of at most kFixCap (its first thread
-    // sorts it), else the group is out of order
+    // an inversion: fine inside a group of at most kFixCap (sorted by its
+    // start), else the group is out of order
     int64_t st = -1;
     for (int i = 1; i <= kFixCap; ++i)
         if (p - i < 0 || (keys[p - i] >> kShortShift) != g) {
@@ -617,28 +650,33 @@ __device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t 
 // ~0 beyond the ends): nothing to do unless p starts a group of two or more
 // records or is an inversion.
 __device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t m, int64_t p, uint64_t kp,
-                                         uint64_t kq, uint64_t kn, bool &long_unsorted) {
+                                         uint64_t kq, uint64_t kn, int64_t chunk_end, uint64_t *defer_list,
+                                         uint32_t *defer_count, int *delta, bool &long_unsorted) {
     const uint64_t g = kp >> kShortShift;
     const bool start = (kq >> kShortShift) != g || p == 0;
     if (start ? (kn >> kShortShift) == g : kp < kq)
-        long_unsorted |= fixup_rare(keys, vals, m, p, kp, kq, start);
+        long_unsorted |= fixup_rare(keys, vals, m, p, kp, start, chunk_end, defer_list, defer_count, delta);
 }
 
 // Each thread takes kFixPer consecutive records (vector loads; a warp covers
-// 32 x kFixPer records at a time); neighbours come from its own registers,
-// from a shuffle at its ends, or from a single load at the warp's ends.
+// 32 x kFixPer records, one de-duplication chunk, at a time); neighbours come
+// from its own registers, from a shuffle at its ends, or from a single load
+// at the warp's ends.  Writes the chunk's count of new values to cnt.
 constexpr int kFixPer = 8;
+constexpr int64_t kFixChunk = 32 * kFixPer;
+static_assert(kFixChunk == kDedupeChunk, "a warp step covers one de-duplication chunk");
 __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
-                                                     uint32_t *vals1, int64_t m, Header *h) {
+                                                     uint32_t *vals1, int64_t m, Header *h, uint32_t *cnt,
+                                                     uint64_t *defer_list) {
     const Plan plan = make_plan(h);
     uint64_t *keys = (plan.passes & 1) ? keys1 : keys0;
     uint32_t *vals = (plan.passes & 1) ? vals1 : vals0;
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    constexpr int64_t kChunk = 32 * kFixPer;
     const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
     bool long_unsorted = false;
-    for (int64_t b = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kChunk; b < m; b += nw * kChunk) {
+    for (int64_t b = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kFixChunk; b < m;
+         b += nw * kFixChunk) {
         const int64_t p0 = b + int64_t(lane) * kFixPer;
         uint64_t k[kFixPer];
         if (vec && p0 + kFixPer <= m) {
@@ -656,16 +694,44 @@ __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *k
         uint64_t prev = __shfl_up_sync(0xffffffffu, k[kFixPer - 1], 1);
         uint64_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
         if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] : ~0ull;
-        if (lane == 31) next = b + kChunk < m ? keys[b + kChunk] : ~0ull;
+        if (lane == 31) next = b + kFixChunk < m ? keys[b + kFixChunk] : ~0ull;
+        int count = 0;
 #pragma unroll
         for (int i = 0; i < kFixPer; ++i) {
             const int64_t p = p0 + i;
-            if (p < m)
-                fixup_at(keys, vals, m, p, k[i], i > 0 ? k[i - 1] : prev, i + 1 < kFixPer ? k[i + 1] : next,
-                         long_unsorted);
+            const uint64_t kq = i > 0 ? k[i - 1] : prev;
+            if (p < m) {
+                count += (p == 0 || k[i] != kq) ? 1 : 0;
+                fixup_at(keys, vals, m, p, k[i], kq, i + 1 < kFixPer ? k[i + 1] : next, b + kFixChunk,
+                         defer_list, &h->defer_count, &count, long_unsorted);
+            }
         }
+        count = int(__reduce_add_sync(0xffffffffu, uint32_t(count)));
+        if (lane == 0) cnt[b / kFixChunk] = uint32_t(count);
     }
     if (long_unsorted) atomicExch(&h->fixup_fallback, 1);
+}
+
+// The second kernel: sorts the groups the fix-up deferred (each reaching
+// across the end of its chunk) and corrects the counts of the chunks its
+// records lie in.
+__global__ void __launch_bounds__(256) k_sort_fixup_deferred(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
+                                                              uint32_t *vals1, int64_t m, const Header *h,
+                                                              uint32_t *cnt, const uint64_t *defer_list) {
+    const Plan plan = make_plan(h);
+    uint64_t *keys = (plan.passes & 1) ? keys1 : keys0;
+    uint32_t *vals = (plan.passes & 1) ? vals1 : vals0;
+    const uint32_t nd = h->defer_count;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += gridDim.x * blockDim.x) {
+        const int64_t p = int64_t(defer_list[q]);
+        const uint64_t g = keys[p] >> kShortShift;
+        int sz = 1;
+        while (sz < kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
+        int8_t dflag[kFixCap];
+        sort_group(keys, vals, p, sz, dflag);  // a zero total may still move counts between chunks
+        for (int i = 1; i < sz; ++i)
+            if (dflag[i]) atomicAdd(&cnt[(p + i) / kFixChunk], uint32_t(int32_t(dflag[i])));
+    }
 }
 
 // ------------------------------------------------------------------ host ---
@@ -775,9 +841,10 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
 // (launch_sort_init), h's histograms complete.  The records end sorted in
 // buffer (passes & 1), unless h->fixup_fallback.
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, cudaStream_t s);
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s);
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s) {
+                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
+                              cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
@@ -785,16 +852,22 @@ cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
         e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s);
         if (e != cudaSuccess) return e;
     }
-    return launch_sort_fixup(keys0, keys1, vals0, vals1, m, h, s);
+    // the deferred groups' list lives in look1, unused after the passes
+    return launch_sort_fixup(keys0, keys1, vals0, vals1, m, h, cnt, look1, s);
 }
 
+// The fix-up and its second kernel; cnt: one word per de-duplication chunk;
+// defer_list: room for one word per chunk.
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, cudaStream_t s) {
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = int64_t(sm_count()) * 8;
     if (blocks > cap) blocks = cap;
-    k_sort_fixup<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h);
+    k_sort_fixup<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sort_fixup_deferred<<<unsigned(sm_count()), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);
     return cudaGetLastError();
 }
 

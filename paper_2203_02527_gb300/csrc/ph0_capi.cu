@@ -19,9 +19,13 @@ cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStre
                              int top_bits = kDefaultTopBits, int64_t sorted_edges = -1,
                              const int32_t *gate = nullptr);
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s);
+                              int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
+                              cudaStream_t s);
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, cudaStream_t s);
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s);
+cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
+                                uint32_t *cnt, const int32_t *gate, cudaStream_t s);
+cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s);
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
                                cudaStream_t s);
@@ -103,20 +107,24 @@ cudaError_t sort_fallback(void *ws, const Layout &L, const float *pts, int64_t n
     if (e == cudaSuccess) e = launch_sort_init(fh, look0, L.tiles, s, t.top_bits, -1, gate);
     if (e == cudaSuccess) e = launch_dist(pts, n, d, ld, k0, v0, fh, s, t.split16, t.tile, gate);
     if (e == cudaSuccess) e = launch_sort_passes(k0, k1, v0, v1, L.m, look0, look1, fh, s);
+    // the fix-up's de-duplication counts no longer hold: count again
+    if (e == cudaSuccess) e = launch_dedupe_count(k0, k1, h, L.m, at<uint32_t>(ws, L.cpref), gate, s);
     return e;
 }
 
 // Step 2 of the whole path (the records of step 1 in buffer 0, h's
 // histograms complete): the short sort (the passes over key bits 16 and up,
-// then a fix-up of the groups they leave; k_sort.cu) and its gated
-// fallback.  The sorted records end in buffer (passes & 1) of h's plan.
+// then a fix-up of the groups they leave, which also counts the new
+// distance values of every de-duplication chunk into cpref; k_sort.cu) and
+// its gated fallback.  The sorted records end in buffer (passes & 1) of h's
+// plan; step 3 then needs only launch_dedupe_scan.
 cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, int32_t d, int64_t ld,
                        const Tune &t, cudaStream_t s) {
     if (L.m <= 0) return cudaSuccess;
     cudaError_t e = launch_sort_short(at<uint64_t>(ws, L.key[0]), at<uint64_t>(ws, L.key[1]),
                                       at<uint32_t>(ws, L.val[0]), at<uint32_t>(ws, L.val[1]), L.m,
                                       at<uint64_t>(ws, L.look[0]), at<uint64_t>(ws, L.look[1]),
-                                      at<Header>(ws, L.hdr), s);
+                                      at<Header>(ws, L.hdr), at<uint32_t>(ws, L.cpref), s);
     if (e != cudaSuccess) return e;
     return sort_fallback(ws, L, pts, n, d, ld, t, s);
 }
@@ -237,7 +245,7 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     return cuda_status(e);
 }
@@ -409,10 +417,10 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
         if (L.m > 0 && p >= kShortSortFirstSlot) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
     }
-    if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, s);
+    if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, cpref, look1, s);
     if (e == cudaSuccess && L.m > 0) e = sort_fallback(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 + kMaxPasses], s);
     if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s, ev[4 + kMaxPasses]);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5 + kMaxPasses], s);
@@ -623,7 +631,7 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     cudaError_t e = begin_call(ws, L, s);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
-    if (e == cudaSuccess) e = launch_dedupe(k0, k1, h, L.m, nullptr, cpref, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int32_t status = PH0_OK;

@@ -84,7 +84,8 @@ struct Header {
     uint32_t nlist[2];           // candidate list lengths (ping-pong)
     int32_t top_bits;            // width of a single top radix pass (8 or 9)
     int32_t fixup_fallback;      // set when the short sort's fix-up meets a long unsorted group
-    uint32_t pad[2];
+    uint32_t defer_count;        // groups the fix-up left to its second kernel
+    uint32_t pad[1];
     int64_t sorted_edges;        // edges sorted: m, or the prefix of the early path
     // class partition of the early path (radix slot kClassSlot): the key
     // bins of its histogram and the classes' bin ranges [bound[c], bound[c+1])
