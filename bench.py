@@ -275,11 +275,12 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
                 "traffic_source": "ncu on the 8192-point cloud, scaled by edges",
                 "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src}
-    # sort init, distances, radix passes from slot 2, fix-up, gated fallback
-    # (sort init, distances, 8 passes: they return at once unless needed),
-    # de-duplication (count, scan), reduction (init, kernel), pivot-order sort
-    # (sort init, key stats, 8 passes), emission
-    launches_per_step = 1 + 1 + 6 + 1 + (1 + 1 + 8) + 2 + 2 + (1 + 1 + 8) + 1
+    # sort init, distances, radix passes from slot 2, fix-up (and its kernel
+    # for deferred groups), gated fallback (sort init, distances, 8 passes,
+    # de-duplication recount: they return at once unless needed), the
+    # de-duplication scan, reduction (init, kernel), pivot-order sort (sort
+    # init, key stats, 8 passes), emission
+    launches_per_step = 1 + 1 + 6 + 2 + (1 + 1 + 8 + 1) + 1 + 2 + (1 + 1 + 8) + 1
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         r, dt, ns, ms_ = time_oracle(x)

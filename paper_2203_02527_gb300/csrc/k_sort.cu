@@ -275,11 +275,12 @@ __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t
 // buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
 // pass's radix) live in look[p&1], and it clears its tile's words in
 // look[(p+1)&1] for the next pass (whose previous user, pass p-1, is done).
-template <int RADIX, int SLOT, bool ALIGNED>
+template <int RADIX, int SLOT, bool ALIGNED, bool PERSIST = false>
 __global__ void __launch_bounds__(kSortThreads, PH0_SORT_MIN_BLOCKS)
 k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
            uint64_t *look0, uint64_t *look1, Header *h) {
     constexpr int T = kSortThreads, IT = kSortItems, TILE = kSortTile, W = T / 32;
+    static_assert(!(ALIGNED && PERSIST), "the persistent instance loads its tiles by cp.async");
     constexpr int DPT = RADIX / T;  // digits per thread
     static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
     static_assert((TILE & (TILE - 1)) == 0, "tile positions are masked to the tile");
@@ -308,226 +309,243 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         cd = ClassDigit{h->part_kmin, h->part_shift, h->part_nc, s_bound};
     }
     __syncthreads();
-    const int64_t tile = S.tile;
-    const int64_t base = tile * TILE;
-    const int valid = int(m - base < TILE ? m - base : TILE);
-    // full tiles arrive in shared memory while the histogram scan below runs:
-    // by two bulk copies when their rows are 16-byte aligned, else (an
-    // instance for unaligned buffers) by each thread's asynchronous copies of
-    // its own items; the ragged last tile uses plain loads
-    const bool bulk = valid == TILE &&
-                      ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15u) == 0;
-    const bool full = ALIGNED ? bulk : valid == TILE;
-    if (bulk && tid == 0) {
-        mbar_expect_tx(&S.mbar, uint32_t(TILE * (sizeof(uint64_t) + sizeof(uint32_t))));
-        bulk_g2s(S.keys, kin + base, uint32_t(TILE * sizeof(uint64_t)), &S.mbar);
-        bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
-    }
-    if constexpr (!ALIGNED) {
-        if (full && !bulk) {
-            const int own = warp * 32 * IT + lane;
+    // PERSIST: the instance launched on fewer CTAs than tiles (passes that
+    // usually return at once), where a CTA takes tiles from the counter until
+    // none is left (every tile it waits on belongs to a CTA that is running);
+    // the others take one tile per CTA
+    for (;;) {
+        const int64_t tile = S.tile;
+        if constexpr (PERSIST) {
+            if (tile >= (m + TILE - 1) / TILE) break;
+        }
+        const int64_t base = tile * TILE;
+        const int valid = int(m - base < TILE ? m - base : TILE);
+        // full tiles arrive in shared memory while the histogram scan below runs:
+        // by two bulk copies when their rows are 16-byte aligned, else (the
+        // instances for unaligned buffers, and the persistent one, whose single
+        // mbarrier is never armed) by each thread's asynchronous copies of its
+        // own items; the ragged last tile uses plain loads
+        const bool bulk = !PERSIST && valid == TILE &&
+                          ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15u) == 0;
+        const bool full = ALIGNED ? bulk : valid == TILE;
+        if (bulk && tid == 0) {
+            mbar_expect_tx(&S.mbar, uint32_t(TILE * (sizeof(uint64_t) + sizeof(uint32_t))));
+            bulk_g2s(S.keys, kin + base, uint32_t(TILE * sizeof(uint64_t)), &S.mbar);
+            bulk_g2s(S.vals_in, vin + base, uint32_t(TILE * sizeof(uint32_t)), &S.mbar);
+        }
+        if constexpr (!ALIGNED) {
+            if (full && !bulk) {
+                const int own = warp * 32 * IT + lane;
+#pragma unroll
+                for (int j = 0; j < IT; ++j) {
+                    cp_async8(&S.keys[own + j * 32], kin + base + own + j * 32);
+                    cp_async4(&S.vals_in[own + j * 32], vin + base + own + j * 32);
+                }
+            }
+        }
+        {  // each warp clears its own counter row (ranking touches only that row)
+            uint32_t *row = reinterpret_cast<uint32_t *>(&S.whist[warp][0]);
+#pragma unroll
+            for (int i = lane; i < RADIX / 2; i += 32) row[i] = 0;
+            __syncwarp();
+        }
+        // digit starts (tile 0 only): exclusive scan of this pass's histogram;
+        // tile 0 folds them into its PREFIX, so later tiles get them by look-back
+        uint32_t bucket[DPT];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) bucket[q] = 0;
+        if (tile == 0) {
+            uint32_t hsum = 0;
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                bucket[q] = h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
+                hsum += bucket[q];
+            }
+            uint32_t tot;
+            uint32_t run = block_excl_scan<T>(hsum, S.scan, tot);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                const uint32_t c = bucket[q];
+                bucket[q] = run;
+                run += c;
+            }
+        }
+
+        // ---- keys (striped within each warp) and stable ranking ----
+        uint64_t k[IT];
+        uint32_t dr[IT];  // digit << 16 | rank within the warp, then the local position
+        const int wloc = warp * 32 * IT;  // the warp's first item within the tile
+        if (full) {  // each thread reads (and later scatters) only its own items
+            if (bulk) {
+                if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
+            } else {
+                cp_async_wait_all();
+            }
+#pragma unroll
+            for (int j = 0; j < IT; ++j) k[j] = S.keys[wloc + j * 32 + lane];
+        } else {
 #pragma unroll
             for (int j = 0; j < IT; ++j) {
-                cp_async8(&S.keys[own + j * 32], kin + base + own + j * 32);
-                cp_async4(&S.vals_in[own + j * 32], vin + base + own + j * 32);
+                const int loc = wloc + j * 32 + lane;
+                k[j] = loc < valid ? kin[base + loc] : 0;
             }
         }
-    }
-    {  // each warp clears its own counter row (ranking touches only that row)
-        uint32_t *row = reinterpret_cast<uint32_t *>(&S.whist[warp][0]);
-#pragma unroll
-        for (int i = lane; i < RADIX / 2; i += 32) row[i] = 0;
-        __syncwarp();
-    }
-    // digit starts (tile 0 only): exclusive scan of this pass's histogram;
-    // tile 0 folds them into its PREFIX, so later tiles get them by look-back
-    uint32_t bucket[DPT];
-#pragma unroll
-    for (int q = 0; q < DPT; ++q) bucket[q] = 0;
-    if (tile == 0) {
-        uint32_t hsum = 0;
-#pragma unroll
-        for (int q = 0; q < DPT; ++q) {
-            bucket[q] = h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
-            hsum += bucket[q];
-        }
-        uint32_t tot;
-        uint32_t run = block_excl_scan<T>(hsum, S.scan, tot);
-#pragma unroll
-        for (int q = 0; q < DPT; ++q) {
-            const uint32_t c = bucket[q];
-            bucket[q] = run;
-            run += c;
-        }
-    }
-
-    // ---- keys (striped within each warp) and stable ranking ----
-    uint64_t k[IT];
-    uint32_t dr[IT];  // digit << 16 | rank within the warp, then the local position
-    const int wloc = warp * 32 * IT;  // the warp's first item within the tile
-    if (full) {  // each thread reads (and later scatters) only its own items
-        if (bulk) {
-            if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
-        } else {
-            cp_async_wait_all();
-        }
-#pragma unroll
-        for (int j = 0; j < IT; ++j) k[j] = S.keys[wloc + j * 32 + lane];
-    } else {
+        const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
         for (int j = 0; j < IT; ++j) {
-            const int loc = wloc + j * 32 + lane;
-            k[j] = loc < valid ? kin[base + loc] : 0;
-        }
-    }
-    const unsigned lt = (1u << lane) - 1u;
+            const uint32_t dj = (full || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan, cd)
+                                                                       : uint32_t(RADIX);
+            // lanes with the same digit.  8-bit digits (raw mantissa bytes, about
+            // uniform: a warp holds ~30 distinct values): intersect one ballot per
+            // digit bit, much faster than a warp match on this GPU; the ragged
+            // tile's sentinel digit RADIX needs one more bit.  The 9-bit top digit
+            // (exponent and leading mantissa bits of d2) is concentrated on few
+            // values, where one warp match beats nine ballots.
+            unsigned peers = 0xffffffffu;
+            if constexpr (RADIX == kMaxRadix) {
+                peers = __match_any_sync(0xffffffffu, dj);
+            } else {
+                constexpr int kBits = 8;
 #pragma unroll
-    for (int j = 0; j < IT; ++j) {
-        const uint32_t dj = (full || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan, cd)
-                                                                   : uint32_t(RADIX);
-        // lanes with the same digit.  8-bit digits (raw mantissa bytes, about
-        // uniform: a warp holds ~30 distinct values): intersect one ballot per
-        // digit bit, much faster than a warp match on this GPU; the ragged
-        // tile's sentinel digit RADIX needs one more bit.  The 9-bit top digit
-        // (exponent and leading mantissa bits of d2) is concentrated on few
-        // values, where one warp match beats nine ballots.
-        unsigned peers = 0xffffffffu;
-        if constexpr (RADIX == kMaxRadix) {
-            peers = __match_any_sync(0xffffffffu, dj);
-        } else {
-            constexpr int kBits = 8;
-#pragma unroll
-            for (int b = 0; b < kBits; ++b) {
-                const bool bit = (dj >> b) & 1u;
-                const unsigned vote = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? vote : ~vote;
+                for (int b = 0; b < kBits; ++b) {
+                    const bool bit = (dj >> b) & 1u;
+                    const unsigned vote = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? vote : ~vote;
+                }
+                if (!full) {
+                    const bool bit = (dj >> kBits) & 1u;
+                    const unsigned vote = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? vote : ~vote;
+                }
             }
-            if (!full) {
-                const bool bit = (dj >> kBits) & 1u;
-                const unsigned vote = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? vote : ~vote;
+            const uint32_t before = __popc(peers & lt);
+            if constexpr (RADIX == kMaxRadix) {
+                // 9-bit digits: the leader alone reads and advances its digit's
+                // count and hands it to its peers (measured faster here)
+                const int leader = __ffs(peers) - 1;
+                uint32_t prior = 0;
+                if (before == 0 && dj < RADIX) {
+                    prior = S.whist[warp][dj];
+                    S.whist[warp][dj] = uint16_t(prior + __popc(peers));
+                }
+                prior = __shfl_sync(0xffffffffu, prior, leader);
+                dr[j] = (dj << 16) | (prior + before);
+                __syncwarp();
+            } else {
+                // 8-bit digits: every lane reads its digit's count, then the leader
+                // advances it (measured faster here)
+                const uint32_t prior = dj < RADIX ? S.whist[warp][dj] : 0u;
+                dr[j] = (dj << 16) | (prior + before);
+                __syncwarp();
+                if (dj < RADIX && before == 0) S.whist[warp][dj] = uint16_t(prior + __popc(peers));
+                __syncwarp();
             }
         }
-        const uint32_t before = __popc(peers & lt);
-        if constexpr (RADIX == kMaxRadix) {
-            // 9-bit digits: the leader alone reads and advances its digit's
-            // count and hands it to its peers (measured faster here)
-            const int leader = __ffs(peers) - 1;
-            uint32_t prior = 0;
-            if (before == 0 && dj < RADIX) {
-                prior = S.whist[warp][dj];
-                S.whist[warp][dj] = uint16_t(prior + __popc(peers));
-            }
-            prior = __shfl_sync(0xffffffffu, prior, leader);
-            dr[j] = (dj << 16) | (prior + before);
-            __syncwarp();
-        } else {
-            // 8-bit digits: every lane reads its digit's count, then the leader
-            // advances it (measured faster here)
-            const uint32_t prior = dj < RADIX ? S.whist[warp][dj] : 0u;
-            dr[j] = (dj << 16) | (prior + before);
-            __syncwarp();
-            if (dj < RADIX && before == 0) S.whist[warp][dj] = uint16_t(prior + __popc(peers));
-            __syncwarp();
-        }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    // ---- per digit: tile total (published at once), then local positions ----
-    uint32_t total[DPT], tsum = 0;
-#pragma unroll
-    for (int q = 0; q < DPT; ++q) {
-        const int d = tid * DPT + q;
-        uint32_t t = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) t += S.whist[w][d];
-        total[q] = t;
-        tsum += t;
-        st_volatile(look + tile * kMaxRadix + d, tile == 0 ? kFlagPrefix | (bucket[q] + t) : kFlagAgg | t);
-    }
-    uint32_t lstart[DPT];
-    {
-        uint32_t tot;
-        uint32_t run = block_excl_scan<T>(tsum, S.scan, tot);
+        // ---- per digit: tile total (published at once), then local positions ----
+        uint32_t total[DPT], tsum = 0;
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             const int d = tid * DPT + q;
-            lstart[q] = run;
-            uint32_t pos = run;  // local position of the first item of each warp, digit d
+            uint32_t t = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t c = S.whist[w][d];
-                S.whist[w][d] = uint16_t(pos);
-                pos += c;
+            for (int w = 0; w < W; ++w) t += S.whist[w][d];
+            total[q] = t;
+            tsum += t;
+            st_volatile(look + tile * kMaxRadix + d, tile == 0 ? kFlagPrefix | (bucket[q] + t) : kFlagAgg | t);
+        }
+        uint32_t lstart[DPT];
+        {
+            uint32_t tot;
+            uint32_t run = block_excl_scan<T>(tsum, S.scan, tot);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                const int d = tid * DPT + q;
+                lstart[q] = run;
+                uint32_t pos = run;  // local position of the first item of each warp, digit d
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint32_t c = S.whist[w][d];
+                    S.whist[w][d] = uint16_t(pos);
+                    pos += c;
+                }
+                run += total[q];
             }
-            run += total[q];
         }
-    }
-    __syncthreads();
-
-    // ---- reorder keys and values by digit in shared memory ----
-#pragma unroll
-    for (int j = 0; j < IT; ++j) {
-        const uint32_t dj = dr[j] >> 16;
-        const int loc = wloc + j * 32 + lane;
-        if (dj < RADIX) {
-            const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
-            S.keys[pos] = k[j];
-            S.vals[pos] = full ? S.vals_in[loc] : vin[base + loc];
-        }
-    }
-
-    // ---- look-back (keys and ranks are dead now), global offsets ----
-#pragma unroll
-    for (int q = 0; q < DPT; ++q) {
-        const int d = tid * DPT + q;
-        uint32_t excl = bucket[q];
-        if (tile != 0) {
-            excl = lookback_window(look + d, tile, h);
-            st_volatile(look + tile * kMaxRadix + d, kFlagPrefix | uint64_t(excl + total[q]));
-        }
-        S.gofs[d] = excl - lstart[q];  // wraps below 0; positions are < 2^31
-    }
-    uint32_t *s_next = S.vals_in;  // dead once every thread has finished the scatter
-    if (hist_top) {
         __syncthreads();
-        for (int i = tid; i < kMaxRadix; i += T) s_next[i] = 0;
-    }
-    __syncthreads();
 
-    // ---- write contiguous runs, one per digit ----
-    const uint32_t m32 = uint32_t(m);  // m < 2^31
-#pragma unroll 4
-    for (int i = tid; i < valid; i += T) {
-        const uint64_t key = S.keys[i];
-        const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan, cd)] + uint32_t(i);
-        if (g >= m32) continue;  // never taken when the counts are consistent
-        kout[g] = key;
-        vout[g] = S.vals[i];
+        // ---- reorder keys and values by digit in shared memory ----
+#pragma unroll
+        for (int j = 0; j < IT; ++j) {
+            const uint32_t dj = dr[j] >> 16;
+            const int loc = wloc + j * 32 + lane;
+            if (dj < RADIX) {
+                const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
+                S.keys[pos] = k[j];
+                S.vals[pos] = full ? S.vals_in[loc] : vin[base + loc];
+            }
+        }
+
+        // ---- look-back (keys and ranks are dead now), global offsets ----
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid * DPT + q;
+            uint32_t excl = bucket[q];
+            if (tile != 0) {
+                excl = lookback_window(look + d, tile, h);
+                st_volatile(look + tile * kMaxRadix + d, kFlagPrefix | uint64_t(excl + total[q]));
+            }
+            S.gofs[d] = excl - lstart[q];  // wraps below 0; positions are < 2^31
+        }
+        uint32_t *s_next = S.vals_in;  // dead once every thread has finished the scatter
         if (hist_top) {
-            const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
-            if (plan.top == 1) {
-                atomicAdd(&s_next[t], 1u);
-            } else {  // two top passes: low and high byte of t
-                atomicAdd(&s_next[t & (kRadix - 1)], 1u);
-                atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
+            __syncthreads();
+            for (int i = tid; i < kMaxRadix; i += T) s_next[i] = 0;
+        }
+        __syncthreads();
+
+        // ---- write contiguous runs, one per digit ----
+        const uint32_t m32 = uint32_t(m);  // m < 2^31
+#pragma unroll 4
+        for (int i = tid; i < valid; i += T) {
+            const uint64_t key = S.keys[i];
+            const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan, cd)] + uint32_t(i);
+            if (g >= m32) continue;  // never taken when the counts are consistent
+            kout[g] = key;
+            vout[g] = S.vals[i];
+            if (hist_top) {
+                const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
+                if (plan.top == 1) {
+                    atomicAdd(&s_next[t], 1u);
+                } else {  // two top passes: low and high byte of t
+                    atomicAdd(&s_next[t & (kRadix - 1)], 1u);
+                    atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
+                }
             }
         }
-    }
-    for (int i = tid; i < kMaxRadix; i += T) look_next[tile * kMaxRadix + i] = 0;
-    if (hist_top) {
-        __syncthreads();
-        for (int i = tid; i < kMaxRadix; i += T) {
-            const uint32_t c = s_next[i];
-            if (!c) continue;
-            constexpr int kNext = SLOT + 1 < kMaxPasses ? SLOT + 1 : kMaxPasses - 1;  // class slot: never
-            if (plan.top == 1) atomicAdd(&h->hist[kNext][i], c);
-            else atomicAdd(&h->hist[kNext + i / kRadix][i % kRadix], c);
+        for (int i = tid; i < kMaxRadix; i += T) look_next[tile * kMaxRadix + i] = 0;
+        if (hist_top) {
+            __syncthreads();
+            for (int i = tid; i < kMaxRadix; i += T) {
+                const uint32_t c = s_next[i];
+                if (!c) continue;
+                constexpr int kNext = SLOT + 1 < kMaxPasses ? SLOT + 1 : kMaxPasses - 1;  // class slot: never
+                if (plan.top == 1) atomicAdd(&h->hist[kNext][i], c);
+                else atomicAdd(&h->hist[kNext + i / kRadix][i % kRadix], c);
+            }
         }
-    }
-    if (tile == 0 && tid == 0) {
-        h->sort_passes = plan.passes;
-        h->key_bits = plan.bits;
+        if (tile == 0 && tid == 0) {
+            h->sort_passes = plan.passes;
+            h->key_bits = plan.bits;
+        }
+        if constexpr (!PERSIST) {
+            break;
+        } else {  // the tile's shared memory is free once every thread is here
+            __syncthreads();
+            if (tid == 0) S.tile = atomicAdd(&h->tile_counter[SLOT], 1u);
+            __syncthreads();
+        }
     }
 }
 
@@ -767,11 +785,16 @@ cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStre
 
 template <int RADIX, int SLOT>
 static cudaError_t set_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(sort_smem<RADIX>()));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(sort_smem<RADIX>()));
+    const int bytes = int(sort_smem<RADIX>());
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if constexpr (SLOT != kClassSlot)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 cudaError_t prepare_sort_kernels() {
@@ -788,9 +811,20 @@ cudaError_t prepare_sort_kernels() {
     return e;
 }
 
+// persist: run the persistent instance on PH0_SORT_MIN_BLOCKS CTAs per SM,
+// for passes that usually return at once (a grid of one CTA per tile costs
+// ~0.1 ms at 131k tiles even then).
 template <int RADIX, int SLOT>
 static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                        int64_t m, uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s) {
+                        int64_t m, uint64_t *look0, uint64_t *look1, Header *h, bool persist, cudaStream_t s) {
+    if constexpr (SLOT != kClassSlot) {
+        if (persist) {
+            const unsigned cap = unsigned(sm_count()) * PH0_SORT_MIN_BLOCKS;
+            k_onesweep<RADIX, SLOT, false, true><<<tiles < cap ? tiles : cap, kSortThreads, sort_smem<RADIX>(), s>>>(
+                keys0, keys1, vals0, vals1, m, look0, look1, h);
+            return;
+        }
+    }
     // tiles arrive by bulk copies only when both buffers' rows are 16-byte aligned
     const bool aligned = ((reinterpret_cast<uintptr_t>(keys0) | reinterpret_cast<uintptr_t>(keys1) |
                            reinterpret_cast<uintptr_t>(vals0) | reinterpret_cast<uintptr_t>(vals1)) & 15u) == 0;
@@ -805,19 +839,21 @@ static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32
 // One pass slot (prepare_sort_kernels() must have run).
 cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                              int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool persist) {
     const unsigned tiles = unsigned((m + kSortTile - 1) / kSortTile);
+#define PH0_SLOT(R, S) launch_slot<R, S>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, persist, s)
     switch (pass) {
-        case 0: launch_slot<kRadix, 0>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 1: launch_slot<kRadix, 1>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 2: launch_slot<kRadix, 2>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 3: launch_slot<kRadix, 3>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 4: launch_slot<kRadix, 4>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 5: launch_slot<kRadix, 5>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 6: launch_slot<kMaxRadix, 6>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        case 7: launch_slot<kRadix, 7>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
-        default: launch_slot<kRadix, kClassSlot>(tiles, keys0, keys1, vals0, vals1, m, look0, look1, h, s); break;
+        case 0: PH0_SLOT(kRadix, 0); break;
+        case 1: PH0_SLOT(kRadix, 1); break;
+        case 2: PH0_SLOT(kRadix, 2); break;
+        case 3: PH0_SLOT(kRadix, 3); break;
+        case 4: PH0_SLOT(kRadix, 4); break;
+        case 5: PH0_SLOT(kRadix, 5); break;
+        case 6: PH0_SLOT(kMaxRadix, 6); break;
+        case 7: PH0_SLOT(kRadix, 7); break;
+        default: PH0_SLOT(kRadix, kClassSlot); break;
     }
+#undef PH0_SLOT
     return cudaGetLastError();
 }
 
@@ -825,12 +861,12 @@ cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, 
 // ends in buffer (passes & 1), which the device records in the header.
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool persist) {
     if (m <= 0) return cudaSuccess;
     cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
     for (int p = 0; p < kMaxPasses; ++p) {
-        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s);
+        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s, persist);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -849,7 +885,8 @@ cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
     cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
     for (int p = kShortFirstSlot; p < kMaxPasses; ++p) {
-        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s);
+        // the last slot works only for keys whose top part needs two passes
+        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s, p == kMaxPasses - 1);
         if (e != cudaSuccess) return e;
     }
     // the deferred groups' list lives in look1, unused after the passes

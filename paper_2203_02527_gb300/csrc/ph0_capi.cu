@@ -32,10 +32,10 @@ cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h,
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
-                               cudaStream_t s);
+                               cudaStream_t s, bool persist = false);
 cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                              int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
-                             cudaStream_t s);
+                             cudaStream_t s, bool persist = false);
 cudaError_t prepare_sort_kernels();
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
@@ -106,7 +106,8 @@ cudaError_t sort_fallback(void *ws, const Layout &L, const float *pts, int64_t n
     cudaError_t e = cudaMemsetAsync(fh, 0, kHeaderBytes, s);
     if (e == cudaSuccess) e = launch_sort_init(fh, look0, L.tiles, s, t.top_bits, -1, gate);
     if (e == cudaSuccess) e = launch_dist(pts, n, d, ld, k0, v0, fh, s, t.split16, t.tile, gate);
-    if (e == cudaSuccess) e = launch_sort_passes(k0, k1, v0, v1, L.m, look0, look1, fh, s);
+    // persistent grids: the passes return at once unless the flag is set
+    if (e == cudaSuccess) e = launch_sort_passes(k0, k1, v0, v1, L.m, look0, look1, fh, s, true);
     // the fix-up's de-duplication counts no longer hold: count again
     if (e == cudaSuccess) e = launch_dedupe_count(k0, k1, h, L.m, at<uint32_t>(ws, L.cpref), gate, s);
     return e;
@@ -405,8 +406,8 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     }
     // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | fix-up, gated fallback | ev[2+P] |
     // dedupe | ev[3+P] | reduce | ev[4+P] | order pivots, emit | ev[5+P]
-    // (P = kMaxPasses; the short sort launches the passes from slot 3 on,
-    // with the buffers swapped; passes that are not needed return at once)
+    // (P = kMaxPasses; the short sort launches the passes from slot 2 on;
+    // passes that are not needed return at once)
     const Tune t(tuning);
     e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
@@ -414,7 +415,8 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
-        if (L.m > 0 && p >= kShortSortFirstSlot) e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s);
+        if (L.m > 0 && p >= kShortSortFirstSlot)  // as launch_sort_short
+            e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s, p == kMaxPasses - 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
     }
     if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, cpref, look1, s);
