@@ -204,35 +204,29 @@ __host__ __device__ __forceinline__ double bits_to_double(uint64_t b) {
 #endif
 }
 
-// The same squared distance with the squares RN(t*t) formed exactly with
-// integers and the running sum s = RN(s + p) taken by the binary64 adder
-// (16 binary64 operations per edge at d = 16 instead of 47).
-__host__ __device__ __forceinline__ uint64_t sq_dist_mixed(const int64_t *xu, const int64_t *xv,
-                                                           const int32_t *g, int d, int su, int sv,
-                                                           const uint32_t *narrow = nullptr) {
-    // `narrow` bit k: every |X| of dimension k is below 2^30, so t fits a
-    // 32-bit signed difference of the low words
-    double s = 0.0;
-    for (int k = 0; k < d; ++k) {
-        double p;
-        if (narrow && ((narrow[k >> 5] >> (k & 31)) & 1u)) {
-            const int32_t t = int32_t(uint32_t(xv[k * sv])) - int32_t(uint32_t(xu[k * su]));
-            p = bits_to_double(square_bits_narrow(uint32_t(t < 0 ? -t : t), g[k]));
-        } else {
-            const int64_t t = xv[k * sv] - xu[k * su];
-            p = to_double(square53(uint64_t(t < 0 ? -t : t), g[k]));
-        }
-        if (k == 0) {
-            s = p;  // 0 + p is exact
-        } else {
-#ifdef __CUDA_ARCH__
-            s = __dadd_rn(s, p);
-#else
-            volatile double sum = s + p;
-            s = sum;
-#endif
-        }
+// RN(t*t) as a binary64 value for t = xv - xu (fixed point in units of
+// 2^g); narrow: every |X| of the dimension is below 2^30, so t fits a 32-bit
+// signed difference of the low words.
+__host__ __device__ __forceinline__ double square_value(int64_t xu, int64_t xv, int32_t g, bool narrow) {
+    if (narrow) {
+        const int32_t t = int32_t(uint32_t(xv)) - int32_t(uint32_t(xu));
+        return bits_to_double(square_bits_narrow(uint32_t(t < 0 ? -t : t), g));
     }
+    const int64_t t = xv - xu;
+    return to_double(square53(uint64_t(t < 0 ? -t : t), g));
+}
+
+// RN(s + p) by the binary64 adder.
+__host__ __device__ __forceinline__ double add_rn(double s, double p) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(s, p);
+#else
+    volatile double sum = s + p;
+    return sum;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t double_bits(double s) {
 #ifdef __CUDA_ARCH__
     return uint64_t(__double_as_longlong(s));
 #else
@@ -240,6 +234,37 @@ __host__ __device__ __forceinline__ uint64_t sq_dist_mixed(const int64_t *xu, co
     __builtin_memcpy(&b, &s, 8);
     return b;
 #endif
+}
+
+// The same squared distance with the squares RN(t*t) formed exactly with
+// integers and the running sum s = RN(s + p) taken by the binary64 adder
+// (16 binary64 operations per edge at d = 16 instead of 47).  `narrow` bit k:
+// dimension k takes the 32-bit square (see square_value).
+__host__ __device__ __forceinline__ uint64_t sq_dist_mixed(const int64_t *xu, const int64_t *xv,
+                                                           const int32_t *g, int d, int su, int sv,
+                                                           const uint32_t *narrow = nullptr) {
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const bool nk = narrow && ((narrow[k >> 5] >> (k & 31)) & 1u);
+        const double p = square_value(xu[k * su], xv[k * sv], g[k], nk);
+        s = k == 0 ? p : add_rn(s, p);  // 0 + p is exact
+    }
+    return double_bits(s);
+}
+
+// sq_dist_mixed for a dimension D <= 32 and strides S known at compile time
+// (the dimension loop unrolled, the narrow bits in one word).
+template <int D, int S>
+__host__ __device__ __forceinline__ uint64_t sq_dist_mixed_ct(const int64_t *xu, const int64_t *xv,
+                                                              const int32_t *g, uint32_t narrow) {
+    static_assert(D >= 1 && D <= 32, "one word of narrow bits");
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const double p = square_value(xu[k * S], xv[k * S], g[k], (narrow >> k) & 1u);
+        s = k == 0 ? p : add_rn(s, p);
+    }
+    return double_bits(s);
 }
 
 }  // namespace emu

@@ -86,11 +86,22 @@ int main(int argc, char **argv) {
                     sq_dist_fixed(&X[size_t(i) * d], &X[size_t(j) * d], g.data(), d, 1, 1, narrow.data());
                 const uint64_t got_m =
                     sq_dist_mixed(&X[size_t(i) * d], &X[size_t(j) * d], g.data(), d, 1, 1, narrow30.data());
+                // the unrolled form of the dimensions compiled in
+                const int64_t *xi = &X[size_t(i) * d], *xj = &X[size_t(j) * d];
+                uint64_t got_c = got_m;
+                switch (d) {
+                    case 2: got_c = sq_dist_mixed_ct<2, 1>(xi, xj, g.data(), narrow30[0]); break;
+                    case 3: got_c = sq_dist_mixed_ct<3, 1>(xi, xj, g.data(), narrow30[0]); break;
+                    case 8: got_c = sq_dist_mixed_ct<8, 1>(xi, xj, g.data(), narrow30[0]); break;
+                    case 16: got_c = sq_dist_mixed_ct<16, 1>(xi, xj, g.data(), narrow30[0]); break;
+                    case 32: got_c = sq_dist_mixed_ct<32, 1>(xi, xj, g.data(), narrow30[0]); break;
+                    default: break;
+                }
                 const double want = ref_d2(&x[size_t(i) * d], &x[size_t(j) * d], d);
                 uint64_t wb;
                 std::memcpy(&wb, &want, 8);
                 ++edges;
-                if (got != wb || got_n != wb || got_m != wb) {
+                if (got != wb || got_n != wb || got_m != wb || got_c != wb) {
                     if (bad < 5) fprintf(stderr, "mismatch tile %ld kind %d d %d (%d,%d): %016llx vs %016llx\n",
                                          t, kind, d, i, j, (unsigned long long)got, (unsigned long long)wb);
                     ++bad;

@@ -1,8 +1,10 @@
 """The integer emulation of the binary64 squared distance used by the CUDA
-distance kernel (csrc/emu64.cuh), compiled for the host, against the host's
-own IEEE binary64 arithmetic on random tiles of many kinds (unit cube, signed,
-integers with exact ties, spread binades, near-equal values, zeros, signed
-zeros).  Exact equality of the bit patterns is required."""
+distance kernel (csrc/emu64.cuh: the all-integer form, the mixed form and its
+unrolled instances for d in {2, 3, 8, 16, 32}), compiled for the host,
+against the host's own IEEE binary64 arithmetic on random tiles of many kinds
+(unit cube, signed, integers with exact ties, spread binades, near-equal
+values, zeros, signed zeros).  Exact equality of the bit patterns is
+required."""
 import os
 import shutil
 import subprocess
