@@ -79,6 +79,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     // point in units of 2^g[k] on the integer path; then g[d], lo[d], hi[d]
     extern __shared__ double s_coord[];
     __shared__ uint32_t s_hist[kLowPasses][kRadix];
+    __shared__ uint32_t s_top[kMaxRadix];  // (key >> kTopShift) mod kMaxRadix
     __shared__ uint64_t s_min[kDistThreads / 32], s_max[kDistThreads / 32];
     __shared__ int s_fixed;
 
@@ -97,6 +98,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     uint32_t *s_narrow30 = s_narrow + (d + 31) / 32;                // [(d+31)/32] span <= 30 bits
 
     for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) (&s_hist[0][0])[b] = 0;
+    for (int b = threadIdx.x; b < kMaxRadix; b += blockDim.x) s_top[b] = 0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
         s_lo[k] = 1 << 30;
         s_hi[k] = -(1 << 30);
@@ -164,6 +166,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         val[e] = (uint32_t(u) << 16) | uint32_t(v);
 #pragma unroll
         for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
+        atomicAdd(&s_top[(kb >> kTopShift) & (kMaxRadix - 1)], 1u);
         kmin = kb < kmin ? kb : kmin;
         kmax = kb > kmax ? kb : kmax;
     };
@@ -216,6 +219,8 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         const uint32_t c = (&s_hist[0][0])[b];
         if (c) atomicAdd(&h->hist[b / kRadix][b % kRadix], c);
     }
+    for (int b = threadIdx.x; b < kMaxRadix; b += blockDim.x)
+        if (s_top[b]) atomicAdd(&h->hist_top_mod[b], s_top[b]);
 }
 
 // Shared memory of a tile: two staged blocks plus g, lo, hi per dimension.

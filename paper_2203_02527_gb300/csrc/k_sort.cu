@@ -19,9 +19,11 @@
 // ballot per digit bit (8-bit digits) or by one warp match (the 9-bit top
 // digit, which is concentrated on few values).  The tile is reordered by
 // digit in shared memory and written out as contiguous runs, one run per
-// digit.  The six low-digit histograms come from the distance kernel; the
-// last low pass histograms the top digit(s) while it writes, so no pass
-// needs an extra read of the keys.  Every wait is bounded.
+// digit.  The distance kernel supplies the six low-digit histograms and a
+// histogram of the top part modulo 512, which is the single top pass's
+// digit histogram rotated by the minimum key's top part; when the top part
+// needs two passes, the last low pass histograms their digits as it writes.
+// So no pass needs an extra read of the keys.  Every wait is bounded.
 //
 // The whole path sorts with the short sort (launch_sort_short): the passes
 // from slot 2 on, then a fix-up of the rare groups of records whose keys
@@ -78,6 +80,7 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int 
     }
     for (int64_t i = tid; i < int64_t(kMaxPasses) * kMaxRadix; i += stride)
         (&h->hist[0][0])[i] = 0;
+    for (int64_t i = tid; i < kMaxRadix; i += stride) h->hist_top_mod[i] = 0;
     for (int64_t i = tid; i < kMaxPasses + 4; i += stride) h->tile_counter[i] = 0;
     for (int64_t i = tid; i < look_words; i += stride) look0[i] = 0;
 }
@@ -86,8 +89,10 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int 
 // the distance kernel (which computes both itself).
 __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ keys, int64_t m, Header *h) {
     __shared__ uint32_t s_hist[kLowPasses][kRadix];
+    __shared__ uint32_t s_top[kMaxRadix];
     __shared__ uint64_t s_min[8], s_max[8];
     for (int i = threadIdx.x; i < kLowPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kMaxRadix; i += blockDim.x) s_top[i] = 0;
     __syncthreads();
     uint64_t kmin = ~0ull, kmax = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
@@ -95,6 +100,7 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
         const uint64_t k = keys[i];
 #pragma unroll
         for (int p = 0; p < kLowPasses; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & (kRadix - 1)], 1u);
+        atomicAdd(&s_top[(k >> kTopShift) & (kMaxRadix - 1)], 1u);
         kmin = k < kmin ? k : kmin;
         kmax = k > kmax ? k : kmax;
     }
@@ -123,6 +129,8 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&h->hist[i / kRadix][i % kRadix], c);
     }
+    for (int i = threadIdx.x; i < kMaxRadix; i += blockDim.x)
+        if (s_top[i]) atomicAdd(&h->hist_top_mod[i], s_top[i]);
 }
 
 // Shared memory of one pass: the tile's keys (input, then in sorted order),
@@ -295,7 +303,8 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     uint32_t *vout = (SLOT & 1) ? vals0 : vals1;
     uint64_t *look = (SLOT & 1) ? look1 : look0;
     uint64_t *look_next = (SLOT & 1) ? look0 : look1;
-    const bool hist_top = SLOT != kClassSlot && plan.top > 0 && SLOT == plan.low - 1;
+    // two top passes: the last low pass histograms their digits as it writes
+    const bool hist_top = SLOT != kClassSlot && plan.top == 2 && SLOT == plan.low - 1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -358,7 +367,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             uint32_t hsum = 0;
 #pragma unroll
             for (int q = 0; q < DPT; ++q) {
-                bucket[q] = h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
+                // a single top pass: its digit t = (key >> kTopShift) - (kmin >> kTopShift)
+                // is below kMaxRadix, so it has count hist_top_mod[(t + kmin >> kTopShift) mod kMaxRadix]
+                bucket[q] = (SLOT == kLowPasses && plan.top == 1)
+                                ? h->hist_top_mod[(uint32_t(tid * DPT + q) + uint32_t(plan.kmin >> kTopShift)) &
+                                                  (kMaxRadix - 1)]
+                                : h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
                 hsum += bucket[q];
             }
             uint32_t tot;
@@ -514,14 +528,10 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             if (g >= m32) continue;  // never taken when the counts are consistent
             kout[g] = key;
             vout[g] = S.vals[i];
-            if (hist_top) {
+            if (hist_top) {  // the two top passes' digits: low and high byte of t
                 const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
-                if (plan.top == 1) {
-                    atomicAdd(&s_next[t], 1u);
-                } else {  // two top passes: low and high byte of t
-                    atomicAdd(&s_next[t & (kRadix - 1)], 1u);
-                    atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
-                }
+                atomicAdd(&s_next[t & (kRadix - 1)], 1u);
+                atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
             }
         }
         for (int i = tid; i < kMaxRadix; i += T) look_next[tile * kMaxRadix + i] = 0;
@@ -530,9 +540,8 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             for (int i = tid; i < kMaxRadix; i += T) {
                 const uint32_t c = s_next[i];
                 if (!c) continue;
-                constexpr int kNext = SLOT + 1 < kMaxPasses ? SLOT + 1 : kMaxPasses - 1;  // class slot: never
-                if (plan.top == 1) atomicAdd(&h->hist[kNext][i], c);
-                else atomicAdd(&h->hist[kNext + i / kRadix][i % kRadix], c);
+                constexpr int kNext = SLOT + 1 < kMaxPasses - 1 ? SLOT + 1 : kMaxPasses - 2;  // class slot: never
+                atomicAdd(&h->hist[kNext + i / kRadix][i % kRadix], c);
             }
         }
         if (tile == 0 && tid == 0) {

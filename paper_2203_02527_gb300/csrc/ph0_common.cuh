@@ -94,6 +94,10 @@ struct Header {
     int32_t part_nc;
     uint32_t part_bound[kPrefixClasses + 1];
     uint32_t hist[kMaxPasses][kMaxRadix];  // digit histogram per radix pass
+    // histogram of (key >> kTopShift) mod kMaxRadix, taken with the low ones:
+    // when the top part spans less than kMaxRadix values (a single top
+    // pass), it is the top digit's histogram rotated by kmin >> kTopShift
+    uint32_t hist_top_mod[kMaxRadix];
 };
 
 constexpr size_t kHeaderBytes = 32768;
