@@ -32,11 +32,11 @@ from paper_2203_02527_gb300 import inputs  # noqa: E402
 from paper_2203_02527_gb300.replicas import job_throughput, max_over_ranks, replica_seed  # noqa: E402
 
 WORKLOAD = "circles32768"
-# DRAM bytes per edge of one radix pass, averaged over the seven passes
-# (dram__bytes_read.sum + dram__bytes_write.sum of k_onesweep on the
+# DRAM bytes per edge of one radix pass, averaged over the five passes of the
+# whole path (dram__bytes_read.sum + dram__bytes_write.sum of k_onesweep on the
 # 8192-point cloud, profiles/kernels_circles8192.md), scaled by edges to a
 # full launch.
-ONESWEEP_TRAFFIC_PER_EDGE = 24.49
+ONESWEEP_TRAFFIC_PER_EDGE = 24.51
 METRIC = "edges sorted+reduced/s at N=32768"
 # bounded sample of the workload for the CPU oracle: every 5th point
 SAMPLE_STRIDE = 5
