@@ -212,6 +212,43 @@ def test_crowded_distances_take_the_complete_sort():
     np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
 
 
+def test_crowded_cross_distances_take_the_complete_sort_on_many_tiles():
+    """Two clusters of 1500 points each, every coordinate within 1e-12 of 0
+    except the second cluster's y = 1: all 2.25M cross distances lie within
+    ~2e-12 of 1, one long group of equal key >> 16 out of order, so the
+    fix-up hands over to the complete sort, whose radix passes (the
+    persistent instance, on fewer CTAs than the 1099 tiles) do real work."""
+    ph0 = _ph0()
+    rng = np.random.default_rng(41)
+    a = rng.random((1500, 3)) * 1e-12
+    b = rng.random((1500, 3)) * 1e-12
+    b[:, 1] = 1.0
+    x = np.concatenate([a, b]).astype(np.float32)
+    ref = oracle.pipeline(x)
+    keys = ref["d2"].view(np.uint64)  # in (u, v) order
+    cross = keys.reshape(-1)[(ref["u"] < 1500) & (ref["v"] >= 1500)]
+    assert len(np.unique(cross >> np.uint64(16))) <= 2 and np.any(np.diff(cross.astype(np.int64)) < 0)
+    assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), ref["bars"])
+
+
+def test_two_top_passes_on_many_tiles():
+    """Uniform points with two duplicated pairs: the zero distance makes the
+    key range's top part span more than 9 bits, so the sort takes two top
+    passes (the second in the persistent instance on the whole path) over
+    4.5M edges (1099 tiles)."""
+    ph0 = _ph0()
+    x = inputs.uniform(3000, 3, seed=42)
+    x[17] = x[2999]
+    x[5] = x[1234]
+    ref = oracle.pipeline(x)
+    keys = ref["d2"].view(np.uint64)
+    assert int(keys.max() >> np.uint64(48)) - int(keys.min() >> np.uint64(48)) >= 512
+    assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), ref["bars"])
+    key, val = ph0.distances(_cuda(x))
+    ph0.sort_pairs(key, val)
+    np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
+
+
 @pytest.mark.parametrize("split,tile,top", [(0, 128, 9), (5, 64, 9), (16, 32, 8), (11, 128, 8)])
 def test_tuning_changes_no_bit(split, tile, top):
     """Every tuning (distance split, tile size, top radix width) gives the
