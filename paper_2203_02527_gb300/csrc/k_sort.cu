@@ -86,8 +86,11 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int 
 }
 
 // Histograms of the six low digits and the key range of keys not produced by
-// the distance kernel (which computes both itself).
-__global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ keys, int64_t m, Header *h) {
+// the distance kernel (which computes both itself); gate: return at once
+// unless *gate is set (a fallback sort that is not needed).
+__global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ keys, int64_t m, Header *h,
+                                                   const int32_t *gate) {
+    if (gate && ld_volatile(gate) == 0) return;
     __shared__ uint32_t s_hist[kLowPasses][kRadix];
     __shared__ uint32_t s_top[kMaxRadix];
     __shared__ uint64_t s_min[8], s_max[8];
@@ -783,12 +786,12 @@ cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s) {
+cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s, const int32_t *gate) {
     if (m <= 0) return cudaSuccess;
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = int64_t(sm_count()) * 8;
     if (blocks > cap) blocks = cap;
-    k_keystats<<<unsigned(blocks), 256, 0, s>>>(keys, m, h);
+    k_keystats<<<unsigned(blocks), 256, 0, s>>>(keys, m, h, gate);
     return cudaGetLastError();
 }
 

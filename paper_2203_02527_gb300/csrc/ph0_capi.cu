@@ -29,7 +29,8 @@ cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Heade
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
                                cudaStream_t s);
-cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s);
+cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s,
+                            const int32_t *gate = nullptr);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
                                cudaStream_t s, bool persist = false);
@@ -350,11 +351,26 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
         const int64_t c0 = cstart[c], seg = cstart[c + 1] - c0;
         if (seg == 0) continue;
         const int64_t stiles = (seg + kSortTile - 1) / kSortTile;
+        uint64_t *sk0 = k1 + c0, *sk1 = k0 + c0;  // the segment's buffers 0 and 1
+        uint32_t *sv0 = v1 + c0, *sv1 = v0 + c0;
         e = cudaMemsetAsync(sh, 0, kHeaderBytes, s);
         if (e == cudaSuccess) e = launch_sort_init(sh, look0, stiles, s, t.top_bits, seg);
-        if (e == cudaSuccess) e = launch_keystats(k1 + c0, seg, sh, s);
-        if (e == cudaSuccess) e = launch_sort_passes(k1 + c0, k0 + c0, v1 + c0, v0 + c0, seg, look0, look1, sh, s);
-        if (e == cudaSuccess) e = launch_copy_if_odd(k1 + c0, k0 + c0, v1 + c0, v0 + c0, seg, sh, s);
+        if (e == cudaSuccess) e = launch_keystats(sk0, seg, sh, s);
+        // the short sort of the whole path on the segment (it is in (u, v)
+        // order within each class, the class pass being stable): the passes
+        // from slot 2, the fix-up (its chunk counts go to cpref, scratch until
+        // the prefix's de-duplication), the result moved to buffer 0
+        for (int p = kShortSortFirstSlot; p < kMaxPasses && e == cudaSuccess; ++p)
+            e = launch_sort_pass(sk0, sk1, sv0, sv1, seg, p, look0, look1, sh, s, p == kMaxPasses - 1);
+        if (e == cudaSuccess) e = launch_sort_fixup(sk0, sk1, sv0, sv1, seg, sh, cpref, look1, s);
+        if (e == cudaSuccess) e = launch_copy_if_odd(sk0, sk1, sv0, sv1, seg, sh, s);
+        // gated on sh->fixup_fallback (a long group out of order): the
+        // complete sort of the segment as it stands, whose equal keys are
+        // still in (u, v) order (the fix-up permutes within groups, stably)
+        if (e == cudaSuccess) e = launch_sort_init(sh, look0, stiles, s, t.top_bits, -1, &sh->fixup_fallback);
+        if (e == cudaSuccess) e = launch_keystats(sk0, seg, sh, s, &sh->fixup_fallback);
+        if (e == cudaSuccess) e = launch_sort_passes(sk0, sk1, sv0, sv1, seg, look0, look1, sh, s, true);
+        if (e == cudaSuccess) e = launch_copy_if_odd(sk0, sk1, sv0, sv1, seg, sh, s);
         if (e != cudaSuccess) return PH0_ECUDA;
         P = c0 + seg;
         // steps 4-5 on the prefix; enough once it holds n-1 pivots

@@ -205,6 +205,8 @@ def test_crowded_distances_take_the_complete_sort():
     assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), want)
     d2 = want["death_sq"]
     assert d2.min() < 2 and d2.max() - d2.min() < 2.0 ** -36
+    # the early path's class sort falls back the same way
+    assert_bars_equal(ph0.barcodes_early(_cuda(x)).numpy(), want)
     # and the plain step sequence agrees
     ref = oracle.pipeline(x)
     key, val = ph0.distances(_cuda(x))
@@ -229,6 +231,9 @@ def test_crowded_cross_distances_take_the_complete_sort_on_many_tiles():
     cross = keys.reshape(-1)[(ref["u"] < 1500) & (ref["v"] >= 1500)]
     assert len(np.unique(cross >> np.uint64(16))) <= 2 and np.any(np.diff(cross.astype(np.int64)) < 0)
     assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), ref["bars"])
+    # the early path sorts the crowded class the same way (its own fallback)
+    early = ph0.barcodes_early(_cuda(x))
+    assert_bars_equal(early.numpy(), ref["bars"])
 
 
 def test_two_top_passes_on_many_tiles():
