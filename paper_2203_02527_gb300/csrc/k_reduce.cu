@@ -49,6 +49,7 @@
 namespace ph0 {
 
 constexpr int kReduceThreads = 512;
+constexpr int kFilterLoads = 4;
 constexpr int kHashSize = 2048;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr uint32_t kDead = 0xffffffffu;
@@ -313,20 +314,33 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         }
         if (tid == 0) s_hcount = 0;
         __syncthreads();
-        // four loads in flight per thread and iteration
-        for (int64_t b = pos0 + int64_t(blockIdx.x) * (4 * kReduceThreads); b < wend; b += 4 * gstride) {
-            uint32_t vq[4];
+        // kFilterLoads 16-byte loads (4 records each) in flight per thread and
+        // iteration: the filter streams the window at a fraction of the
+        // bandwidth otherwise (it is bound by the bytes in flight)
+        const bool vec = ((reinterpret_cast<uintptr_t>(val + pos0) & 15u) == 0);
+        constexpr int kSpan = kFilterLoads * 4 * kReduceThreads;  // records per CTA and iteration
+        for (int64_t b = pos0 + int64_t(blockIdx.x) * kSpan; b < wend; b += G * kSpan) {
+            uint32_t vq[kFilterLoads * 4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t p = b + q * kReduceThreads + tid;
-                vq[q] = p < wend ? val[p] : 0u;
+            for (int q = 0; q < kFilterLoads; ++q) {
+                const int64_t p0 = b + (int64_t(q) * kReduceThreads + tid) * 4;
+                if (vec && p0 + 4 <= wend) {
+                    const uint4 w = *reinterpret_cast<const uint4 *>(val + p0);
+                    vq[4 * q] = w.x;
+                    vq[4 * q + 1] = w.y;
+                    vq[4 * q + 2] = w.z;
+                    vq[4 * q + 3] = w.w;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vq[4 * q + r] = p0 + r < wend ? val[p0 + r] : 0u;
+                }
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t p = b + q * kReduceThreads + tid;
+            for (int qr = 0; qr < kFilterLoads * 4; ++qr) {
+                const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
                 bool direct = false;
                 if (p < wend) {
-                    uint32_t vv = vq[q];
+                    uint32_t vv = vq[qr];
                     if ((vv >> 16) >= n || (vv & 0xffffu) >= n) {  // corrupt input: never index past n
                         set_status(h, PH0_EINTERNAL);
                         vv = 0;
