@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         if (tid == 0) s_hcount = 0;
         __syncthreads();
         // kFilterLoads 16-byte loads (4 records each) in flight per thread and
-        // iteration: the filter streams the window at a fraction of the
-        // bandwidth otherwise (it is bound by the bytes in flight)
+        // iteration (one CTA per SM: the filter is bound by the bytes in
+        // flight and the work per record)
         const bool vec = ((reinterpret_cast<uintptr_t>(val + pos0) & 15u) == 0);
         constexpr int kSpan = kFilterLoads * 4 * kReduceThreads;  // records per CTA and iteration
         for (int64_t b = pos0 + int64_t(blockIdx.x) * kSpan; b < wend; b += G * kSpan) {
@@ -335,38 +335,62 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                     for (int r = 0; r < 4; ++r) vq[4 * q + r] = p0 + r < wend ? val[p0 + r] : 0u;
                 }
             }
+            // the endpoints' snapshot roots of every record first (bit qr of
+            // `differ`: different roots); late windows have almost none, and
+            // then the warp skips the candidate handling below at once
+            uint32_t differ = 0;
 #pragma unroll
             for (int qr = 0; qr < kFilterLoads * 4; ++qr) {
                 const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
-                bool direct = false;
                 if (p < wend) {
                     uint32_t vv = vq[qr];
                     if ((vv >> 16) >= n || (vv & 0xffffu) >= n) {  // corrupt input: never index past n
                         set_status(h, PH0_EINTERNAL);
-                        vv = 0;
+                        vq[qr] = vv = 0;
                     }
+                    if (s_comp[vv >> 16] != s_comp[vv & 0xffffu]) differ |= 1u << qr;
+                }
+            }
+            if (!__any_sync(0xffffffffu, differ != 0)) continue;
+            uint32_t direct = 0;  // bit qr: the record goes to the candidate list as it is
+#pragma unroll
+            for (int qr = 0; qr < kFilterLoads * 4; ++qr) {
+                const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
+                if ((differ >> qr) & 1u) {
+                    const uint32_t vv = vq[qr];
                     const uint32_t cu = s_comp[vv >> 16], cv = s_comp[vv & 0xffffu];
-                    if (cu != cv) {
-                        const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
-                        const uint32_t pair = (lo << 16) | hi;
-                        bool done = false;
-                        if (*(volatile uint32_t *)&s_hcount < kHashSize / 2) {
-                            const uint32_t hs = (pair * 2654435761u) >> 21;  // 11 bits
-                            for (int pr = 0; pr < 8; ++pr) {
-                                const uint32_t slot = (hs + pr) & (kHashSize - 1);
-                                const uint32_t old = atomicCAS(&s_hkey[slot], kEmpty, pair);
+                    const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
+                    const uint32_t pair = (lo << 16) | hi;
+                    bool done = false;
+                    if (*(volatile uint32_t *)&s_hcount < kHashSize / 2) {
+                        const uint32_t hs = (pair * 2654435761u) >> 21;  // 11 bits
+                        for (int pr = 0; pr < 8; ++pr) {
+                            const uint32_t slot = (hs + pr) & (kHashSize - 1);
+                            // a slot keeps its pair for the whole window, so a plain
+                            // read that finds it needs no CAS; the minimum only
+                            // falls, so a plain read at or below p needs no atomic
+                            // (every record of a pair hits one slot: no contention)
+                            uint32_t old = *(volatile uint32_t *)&s_hkey[slot];
+                            if (old != pair) {
+                                old = atomicCAS(&s_hkey[slot], kEmpty, pair);
                                 if (old == kEmpty) atomicAdd(&s_hcount, 1u);
-                                if (old == kEmpty || old == pair) {
+                            }
+                            if (old == kEmpty || old == pair) {
+                                if (*(volatile uint32_t *)&s_hval[slot] > uint32_t(p))
                                     atomicMin(&s_hval[slot], uint32_t(p));
-                                    done = true;
-                                    break;
-                                }
+                                done = true;
+                                break;
                             }
                         }
-                        direct = !done;
                     }
+                    if (!done) direct |= 1u << qr;
                 }
-                warp_append(direct, uint32_t(p), A.cand0, &h->nlist[0]);
+            }
+            if (!__any_sync(0xffffffffu, direct != 0)) continue;
+#pragma unroll
+            for (int qr = 0; qr < kFilterLoads * 4; ++qr) {
+                const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
+                warp_append((direct >> qr) & 1u, uint32_t(p), A.cand0, &h->nlist[0]);
             }
         }
         __syncthreads();
