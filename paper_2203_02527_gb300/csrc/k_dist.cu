@@ -4,22 +4,25 @@
 //
 // One CTA per tile of the upper triangle: a block of BT row points (u) by a
 // block of BT column points (v), v-block >= u-block.  The binary32
-// coordinates of both blocks are staged in shared memory as binary64,
-// dimension-major, so that a warp reads 32 consecutive v (no bank conflicts)
-// and the u coordinate is a broadcast.  A warp writes 32 consecutive edges of
-// one row u, so the key (8 B) and val (4 B) stores are coalesced.
+// coordinates of both blocks are staged in shared memory, dimension-major
+// (as binary64, or as fixed-point integers, see below), so that a warp reads
+// 32 consecutive v (no bank conflicts) and the u coordinate is a broadcast.
+// A warp writes 32 consecutive edges of one row u, so the key (8 B) and val
+// (4 B) stores are coalesced.
 //
 // The arithmetic: when, in every dimension, the tile's coordinates are exact
 // integers times a common power of two with magnitudes below 2^52 (checked
-// per tile), the rounded binary64 sequence is computed bit-identically with
-// integer arithmetic (emu64.cuh) for half of the tile's rows and with the
-// binary64 units for the other half, because the binary64 units of this GPU
-// run at 1/64 of the integer rate and the two pipes overlap; otherwise the
-// whole tile uses the binary64 units.
+// per tile), the rounded binary64 sequence is computed bit-identically from
+// those integers (emu64.cuh): each square RN(t*t) exactly with integer
+// operations and the running sum on the binary64 adder (the "mixed" form),
+// or all of it with integer operations; the binary64 units of this GPU run
+// at 1/64 of the integer rate, so the squares go to the integer units and
+// only the d-1 additions per edge to the binary64 adder.  Otherwise the
+// whole tile uses the literal binary64 sequence.
 //
 // Fused: the histograms of the six low 8-bit key digits (the low radix
-// passes), the min and max key (the sort's bit range), and the finiteness
-// check of the input.
+// passes) and of the top part of the key modulo 512, the min and max key
+// (the sort's bit range), and the finiteness check of the input.
 #include "emu64.cuh"
 #include "ph0_common.cuh"
 
