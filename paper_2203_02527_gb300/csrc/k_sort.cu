@@ -371,7 +371,8 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 #pragma unroll
             for (int q = 0; q < DPT; ++q) {
                 // a single top pass: its digit t = (key >> kTopShift) - (kmin >> kTopShift)
-                // is below kMaxRadix, so it has count hist_top_mod[(t + kmin >> kTopShift) mod kMaxRadix]
+                // is below kMaxRadix, so its count is hist_top_mod[r] with
+                // r = (t + (kmin >> kTopShift)) mod kMaxRadix (no other digit maps to r)
                 bucket[q] = (SLOT == kLowPasses && plan.top == 1)
                                 ? h->hist_top_mod[(uint32_t(tid * DPT + q) + uint32_t(plan.kmin >> kTopShift)) &
                                                   (kMaxRadix - 1)]
