@@ -254,7 +254,11 @@ __host__ __device__ __forceinline__ Plan make_plan(uint64_t kmin, uint64_t kmax,
     if (kmax < kmin) kmax = kmin;  // no keys
     const int hi = bitlen64(kmin ^ kmax);
     if (hi <= kTopShift) {
-        p.low = (hi + kRadixBits - 1) / kRadixBits;
+        // at least two low passes when any bit varies: the short sort, which
+        // starts at slot 2, then leaves the records in buffer (passes & 1) =
+        // 0 where it ran no pass (slot 1 sorts equal bits: a stable no-op)
+        const int low = (hi + kRadixBits - 1) / kRadixBits;
+        p.low = hi == 0 ? 0 : (low < 2 ? 2 : low);
         p.top = 0;
         p.bits = hi;
     } else {

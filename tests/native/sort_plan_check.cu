@@ -43,6 +43,8 @@ static bool check(uint64_t kmin, uint64_t kmax, int top_bits, std::mt19937_64 &r
     if (p.top == 0 && hi > kTopShift) return false;
     if (p.top > 0 && p.low != kLowPasses) return false;
     if (p.passes != p.low + p.top || p.passes > kMaxPasses) return false;
+    // never a single pass: the short sort (from slot 2) relies on it
+    if (p.passes == 1) return false;
     // random keys in [kmin, kmax], both ends included
     const int n = 3000;
     std::vector<std::pair<uint64_t, uint32_t>> rec(n);

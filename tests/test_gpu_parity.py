@@ -214,6 +214,27 @@ def test_crowded_distances_take_the_complete_sort():
     np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
 
 
+def test_distances_within_a_few_units_in_the_last_place():
+    """Simplex vertices with off-diagonal perturbations of ~1e-14: all 190
+    squared distances lie within 2^8 units in the last place of each other
+    (only the lowest key byte varies), so the plan has no more than the two
+    low passes that the short sort skips; the records stay where the
+    distance kernel wrote them and the fix-up sorts them (or hands over to
+    the complete sort)."""
+    ph0 = _ph0()
+    rng = np.random.default_rng(5)
+    x = (np.eye(20) + rng.random((20, 20)) * 1e-14).astype(np.float32)
+    np.fill_diagonal(x, 1.0)
+    ref = oracle.pipeline(x)
+    keys = ref["d2"].view(np.uint64)
+    assert 0 < int(keys.min() ^ keys.max()).bit_length() <= 8
+    assert_bars_equal(ph0.barcodes(_cuda(x)).numpy(), ref["bars"])
+    assert_bars_equal(ph0.barcodes_early(_cuda(x)).numpy(), ref["bars"])
+    key, val = ph0.distances(_cuda(x))
+    ph0.sort_pairs(key, val)
+    np.testing.assert_array_equal(_u64(key), ref["d2_sorted"].view(np.uint64))
+
+
 def test_crowded_cross_distances_take_the_complete_sort_on_many_tiles():
     """Two clusters of 1500 points each, every coordinate within 1e-12 of 0
     except the second cluster's y = 1: all 2.25M cross distances lie within
