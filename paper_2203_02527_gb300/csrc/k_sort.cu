@@ -562,16 +562,20 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     }
 }
 
-// After the passes: if the sorted data ended in buffer 1 (odd pass count),
-// copy it into buffer 0 (used when the caller's buffer must hold the result).
-__global__ void k_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
-                              const uint32_t *vals1, int64_t m, const Header *h) {
+// After the passes: copy (src -> dst) the records when h's plan has a pass
+// count of the given parity (-1: any) and, if gate is given, *gate is set.
+// With parity 1, src = buffer 1 and dst = buffer 0, it moves the sorted data
+// into buffer 0 (when the caller's buffer must hold the result).
+__global__ void k_copy_parity(uint64_t *keys_dst, const uint64_t *keys_src, uint32_t *vals_dst,
+                              const uint32_t *vals_src, int64_t m, const Header *h, int parity,
+                              const int32_t *gate) {
+    if (gate && ld_volatile(gate) == 0) return;
     const Plan plan = make_plan(h);
-    if ((plan.passes & 1) == 0) return;
+    if (parity >= 0 && (plan.passes & 1) != parity) return;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += int64_t(gridDim.x) * blockDim.x) {
-        keys0[i] = keys1[i];
-        vals0[i] = vals1[i];
+        keys_dst[i] = keys_src[i];
+        vals_dst[i] = vals_src[i];
     }
 }
 
@@ -921,14 +925,20 @@ cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
-                               const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s) {
+cudaError_t launch_copy_parity(uint64_t *keys_dst, const uint64_t *keys_src, uint32_t *vals_dst,
+                               const uint32_t *vals_src, int64_t m, const Header *h, int parity,
+                               const int32_t *gate, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = int64_t(sm_count()) * 8;
     if (blocks > cap) blocks = cap;
-    k_copy_if_odd<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h);
+    k_copy_parity<<<unsigned(blocks), 256, 0, s>>>(keys_dst, keys_src, vals_dst, vals_src, m, h, parity, gate);
     return cudaGetLastError();
+}
+
+cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
+                               const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s) {
+    return launch_copy_parity(keys0, keys1, vals0, vals1, m, h, 1, nullptr, s);
 }
 
 }  // namespace ph0

@@ -38,6 +38,9 @@ cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, 
                              int64_t m, int pass, uint64_t *look0, uint64_t *look1, Header *h,
                              cudaStream_t s, bool persist = false);
 cudaError_t prepare_sort_kernels();
+cudaError_t launch_copy_parity(uint64_t *keys_dst, const uint64_t *keys_src, uint32_t *vals_dst,
+                               const uint32_t *vals_src, int64_t m, const Header *h, int parity,
+                               const int32_t *gate, cudaStream_t s);
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s);
 cudaError_t launch_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h,
@@ -343,8 +346,9 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     if (e != cudaSuccess) return PH0_ECUDA;
     if (pst != PH0_OK) return pst;
 
-    // rounds: sort the next class in place in buffer 1 (buffer 0, no longer
-    // needed, is the scratch), then run the reduction on the sorted prefix
+    // rounds: sort the next class (in buffer 1, where the class pass put it)
+    // into buffer 0, no longer needed otherwise, where the sorted prefix
+    // grows; then run the reduction on the sorted prefix
     int64_t P = 0;
     bool done = false;
     for (int c = 0; c < nc && !done; ++c) {
@@ -359,22 +363,27 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
         // the short sort of the whole path on the segment (it is in (u, v)
         // order within each class, the class pass being stable): the passes
         // from slot 2, the fix-up (its chunk counts go to cpref, scratch until
-        // the prefix's de-duplication), the result moved to buffer 0
+        // the prefix's de-duplication); the sorted prefix grows in buffer 0 of
+        // the call, the segment's buffer 1, where an odd pass count (five
+        // from slot 2, as a rule) leaves it: else one copy moves it there
         for (int p = kShortSortFirstSlot; p < kMaxPasses && e == cudaSuccess; ++p)
             e = launch_sort_pass(sk0, sk1, sv0, sv1, seg, p, look0, look1, sh, s, p == kMaxPasses - 1);
         if (e == cudaSuccess) e = launch_sort_fixup(sk0, sk1, sv0, sv1, seg, sh, cpref, look1, s);
-        if (e == cudaSuccess) e = launch_copy_if_odd(sk0, sk1, sv0, sv1, seg, sh, s);
+        if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, seg, sh, 0, nullptr, s);
         // gated on sh->fixup_fallback (a long group out of order): the
         // complete sort of the segment as it stands, whose equal keys are
-        // still in (u, v) order (the fix-up permutes within groups, stably)
-        if (e == cudaSuccess) e = launch_sort_init(sh, look0, stiles, s, t.top_bits, -1, &sh->fixup_fallback);
-        if (e == cudaSuccess) e = launch_keystats(sk0, seg, sh, s, &sh->fixup_fallback);
+        // still in (u, v) order (the fix-up permutes within groups, stably),
+        // from the segment's buffer 0 and back into its buffer 1
+        const int32_t *fb = &sh->fixup_fallback;
+        if (e == cudaSuccess) e = launch_copy_parity(sk0, sk1, sv0, sv1, seg, sh, -1, fb, s);
+        if (e == cudaSuccess) e = launch_sort_init(sh, look0, stiles, s, t.top_bits, -1, fb);
+        if (e == cudaSuccess) e = launch_keystats(sk0, seg, sh, s, fb);
         if (e == cudaSuccess) e = launch_sort_passes(sk0, sk1, sv0, sv1, seg, look0, look1, sh, s, true);
-        if (e == cudaSuccess) e = launch_copy_if_odd(sk0, sk1, sv0, sv1, seg, sh, s);
+        if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, seg, sh, 0, fb, s);
         if (e != cudaSuccess) return PH0_ECUDA;
         P = c0 + seg;
         // steps 4-5 on the prefix; enough once it holds n-1 pivots
-        e = run_reduce(ws, L, n, P, v1, v1, nullptr, s);
+        e = run_reduce(ws, L, n, P, v0, v0, nullptr, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         Header hh;
         if (e == cudaSuccess) e = cudaMemcpy(&hh, h, sizeof(Header), cudaMemcpyDeviceToHost);
@@ -388,8 +397,8 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     if (!done) return PH0_EINTERNAL;  // all edges sorted: the reduction always completes
 
     // step 3 on the prefix (count mode) and the read-out; then the prefix length
-    e = launch_dedupe(k1, k1, nullptr, P, nullptr, cpref, dlook, h, s);
-    if (e == cudaSuccess) e = order_and_emit(ws, L, n, P, v1, v1, k1, k1, nullptr, nullptr, cpref, bars_dev, s);
+    e = launch_dedupe(k0, k0, nullptr, P, nullptr, cpref, dlook, h, s);
+    if (e == cudaSuccess) e = order_and_emit(ws, L, n, P, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h->sorted_edges, &P, sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return PH0_ECUDA;
