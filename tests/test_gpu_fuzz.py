@@ -39,7 +39,7 @@ def _cloud(rng: np.random.Generator, kind: int) -> np.ndarray:
         x = np.concatenate([a, b])
     elif kind == 7:  # simplex vertices with tiny off-diagonal perturbations
         m = min(n, 200)
-        x = np.eye(m) + rng.random((m, m)) * float(rng.choice([1e-12, 1e-10, 1e-8]))
+        x = np.eye(m) + rng.random((m, m)) * float(rng.choice([3e-16, 1e-15, 1e-14, 1e-12, 1e-10, 1e-8]))
         np.fill_diagonal(x, 1.0)
     else:
         x = inputs.noisy_circles(max(1, n // 4), 4, max(d, 2), noise=float(rng.uniform(0.0, 0.05)), seed=s)
