@@ -73,7 +73,8 @@ typedef struct {
 /* Counters of the last call on a workspace, read back by ph0_finish(). */
 typedef struct {
     int32_t status;          /* ph0_status of the device-side work            */
-    int32_t sort_passes;     /* radix passes that moved data                  */
+    int32_t sort_passes;     /* radix passes of the key range's plan (the     *
+                              * whole path runs those from slot 2 on)         */
     int32_t key_bits;        /* varying key bits sorted                       */
     int32_t windows;         /* reduction windows processed                   */
     int64_t n_distinct;      /* |D|                                           */
