@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2203_02527_gb300 import inputs
-from tests import pins
+from tests import golden, pins
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -82,6 +82,18 @@ def test_steps_bit_exact(case):
     assert_bars_equal(whole.numpy(), ref["bars"])
     assert whole.stats["n_distinct"] == ref["n_distinct"]
     assert whole.stats["n_bars"] == n - 1
+
+
+@pytest.mark.parametrize("name", sorted(golden.FIXTURES))
+def test_stored_bars(name):
+    """The GPU paths against the stored barcodes (no oracle at test time)."""
+    ph0 = _ph0()
+    meta, lines = golden.stored(name)
+    pts = _cuda(golden.points(name))
+    whole = ph0.barcodes(pts)
+    assert golden.bar_lines(whole.numpy()) == lines
+    assert whole.stats["n_distinct"] == meta["distinct_distances"]
+    assert golden.bar_lines(ph0.barcodes_early(pts).numpy()) == lines
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 31, 32, 33, 64, 65, 127, 129, 255, 257])
