@@ -423,15 +423,19 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             if constexpr (RADIX == kMaxRadix) {
                 peers = __match_any_sync(0xffffffffu, dj);
             } else {
-                constexpr int kBits = 8;
+                // the class digit (at most kPrefixClasses values) has 3 bits
+                constexpr int kBits = SLOT == kClassSlot ? 3 : 8;
+                static_assert(kPrefixClasses <= 8, "class digits fit 3 bits");
 #pragma unroll
                 for (int b = 0; b < kBits; ++b) {
                     const bool bit = (dj >> b) & 1u;
                     const unsigned vote = __ballot_sync(0xffffffffu, bit);
                     peers &= bit ? vote : ~vote;
                 }
-                if (!full) {
-                    const bool bit = (dj >> kBits) & 1u;
+                if (!full) {  // the sentinel digit RADIX of the ragged tile
+                    bool bit;
+                    if constexpr (SLOT == kClassSlot) bit = dj >= uint32_t(1u << kBits);
+                    else bit = (dj >> kBits) & 1u;
                     const unsigned vote = __ballot_sync(0xffffffffu, bit);
                     peers &= bit ? vote : ~vote;
                 }
