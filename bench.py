@@ -15,6 +15,7 @@ sample of the same workload on the host cores (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,11 +33,21 @@ from paper_2203_02527_gb300 import inputs  # noqa: E402
 from paper_2203_02527_gb300.replicas import job_throughput, max_over_ranks, replica_seed  # noqa: E402
 
 WORKLOAD = "circles32768"
-# DRAM bytes per edge of one radix pass, averaged over the five passes of the
-# whole path (dram__bytes_read.sum + dram__bytes_write.sum of k_onesweep on the
-# 8192-point cloud, profiles/kernels_circles8192.md), scaled by edges to a
-# full launch.
-ONESWEEP_TRAFFIC_PER_EDGE = 24.51
+# DRAM bytes per edge (dram__bytes_read.sum + dram__bytes_write.sum over the
+# launch, divided by its edges) of the kernels of the distance+sort phase,
+# from one ncu capture on the 8192-point circles cloud
+# (profiles/kernels_circles8192.md), scaled by edges to the benchmark cloud:
+# the distance kernel, one radix pass (mean of the passes), the fix-up.
+PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 24.51, "k_sort_fixup": 8.16}
+ONESWEEP_TRAFFIC_PER_EDGE = PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
+# the algorithmic floor of the phase (steps 1-3): write the records (12 B),
+# read and write them once to sort (24 B), read the keys and write a (12 B)
+PHASE_FLOOR_PER_EDGE = 48.0
+# binary64 additions per SM per clock: the nominal rate (1.25 TFLOP/s counting
+# a fused multiply-add as 2, at 152 SMs and 2.07 GHz) and the rate a probe
+# kernel of dependent-free additions measured on GB300
+ADDS_PER_SM_CLK_NOMINAL = 2.0
+ADDS_PER_SM_CLK_MEASURED = 1.6
 METRIC = "edges sorted+reduced/s at N=32768"
 # bounded sample of the workload for the CPU oracle: every 5th point
 SAMPLE_STRIDE = 5
@@ -219,6 +230,7 @@ def run_ours(args, rank, world, local_rank):
         dpts = host_pts.to(dev, non_blocking=True)
         b = ph0.barcodes(dpts, ws)
         host_bars = b.raw.to("cpu")
+        host_inf = b.inf_raw.to("cpu")  # the bar that never dies
         e1.record()
         e1.synchronize()
         if i >= args.warmup:
@@ -270,32 +282,54 @@ def run_ours(args, rank, world, local_rank):
                  "launches": len(ran), "ms_per_launch": per_pass_ms}
     # the distance kernel: its binding unit is the binary64 adder, which takes
     # the d-1 running-sum additions per edge (the exact squares are formed on
-    # the integer ALU); peak = 2 binary64 operations per SM per clock
+    # the integer ALU); peak = additions per SM per clock x the device's SMs x
+    # the SM clock sampled during the timed region
+    clocks = sampler.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_hz = (clocks["sm_mhz"] or 2070.0) * 1e6
     adds = max(d - 1, 1) * m
-    adder_peak = 152 * 2 * 2.07e9
+    adder_peak = sms * ADDS_PER_SM_CLK_NOMINAL * clk_hz
+    adder_meas = sms * ADDS_PER_SM_CLK_MEASURED * clk_hz
     achieved = adds / (stages["dist_ms"] * 1e-3) if stages["dist_ms"] > 0 else 0.0
     roof_dist = {"kernel": "k_dist", "bound": "alu", "achieved": achieved / 1e12, "peak": adder_peak / 1e12,
                  "unit": "T binary64 additions/s", "frac": achieved / adder_peak, "traffic": None,
                  "algorithmic_ops": adds,
-                 "peak_source": "derived: 2 binary64 operations per SM per clock x 152 SMs x 2.07 GHz"}
+                 "frac_of_probe_rate": achieved / adder_meas,
+                 "peak_source": (f"derived: {ADDS_PER_SM_CLK_NOMINAL:g} binary64 additions per SM per clock "
+                                 f"(nominal) x {sms} SMs x {clk_hz / 1e9:.3f} GHz (median sampled SM clock); "
+                                 f"frac_of_probe_rate uses the {ADDS_PER_SM_CLK_MEASURED:g} per SM per clock "
+                                 f"a probe measured")}
     # the dominant kernel by time: the radix passes together, or the distances
     if stages["dist_ms"] >= per_pass_ms * max(len(ran), 1):
         roof, roof_other = roof_dist, roof_sort
     else:
         roof, roof_other = roof_sort, roof_dist
+    # the distance+sort phase (steps 1-2 and the counts of step 3): DRAM bytes
+    # of its kernels (ncu, scaled by edges) over its device time, against the
+    # copy peak; and the algorithmic floor's bytes over the same time
+    phase_ms = stages["dist_ms"] + stages["sort_ms"]
+    phase_bytes = m * (PHASE_TRAFFIC_PER_EDGE["k_dist"] + len(ran) * PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
+                       + PHASE_TRAFFIC_PER_EDGE["k_sort_fixup"])
+    phase = {"kernels": "k_dist, k_onesweep x%d, k_sort_fixup" % len(ran), "ms": phase_ms,
+             "traffic": phase_bytes, "traffic_per_edge": phase_bytes / m,
+             "achieved": phase_bytes / (phase_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+             "frac": phase_bytes / (phase_ms * 1e-3) / 1e9 / hbm,
+             "floor_per_edge": PHASE_FLOOR_PER_EDGE,
+             "floor_frac": PHASE_FLOOR_PER_EDGE * m / (phase_ms * 1e-3) / 1e9 / hbm,
+             "traffic_source": "ncu dram bytes per edge of each kernel on the 8192-point cloud, scaled by edges",
+             "peak_source": hbm_src}
     # sort init, distances, radix passes from slot 2, fix-up (and its kernel
     # for deferred groups), gated fallback (sort init, distances, 8 passes,
     # de-duplication recount: they return at once unless needed), the
     # de-duplication scan, reduction (init, kernel), pivot-order sort (sort
-    # init, key stats, 8 passes), emission
-    launches_per_step = 1 + 1 + 6 + 2 + (1 + 1 + 8 + 1) + 1 + 2 + (1 + 1 + 8) + 1
+    # init, key stats, 8 passes), emission, the infinite bar
+    launches_per_step = 1 + 1 + 6 + 2 + (1 + 1 + 8 + 1) + 1 + 2 + (1 + 1 + 8) + 1 + 1
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         r, dt, ns, ms_ = time_oracle(x)
         cpu = {"value": r, "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": f"every {SAMPLE_STRIDE}th point of the cloud: N={ns}, {ms_} edges, "
                          f"{dt:.1f} s single-threaded"}
-    clocks = sampler.summary()
     serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
     line = {
         "metric": METRIC, "value": job_throughput(m, world, ms), "unit": "edges/s",
@@ -309,10 +343,11 @@ def run_ours(args, rank, world, local_rank):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
         "e2e": {"value": job_throughput(m, world, e2e), "unit": "edges/s",
-                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(host_bars.numel())},
+                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(host_bars.numel() + host_inf.numel())},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "roofline_other": roof_other,
+        "phase": phase,
         "cpu_baseline": cpu,
         "tuning": tuning,
         "serving": serving,
@@ -346,20 +381,38 @@ def run_serving(args, dev):
     for x in clouds[:20]:
         ph0.barcodes(torch.from_numpy(x).to(dev), ws)
     torch.cuda.synchronize()
-    lat, plain_bars = [], {}
+
+    def plain_call(x):
+        pts = torch.from_numpy(x).pin_memory().to(dev, non_blocking=True)
+        return ph0.barcodes(pts, ws).raw.to("cpu")
+
+    lat, plain_hash = [], {}
     t0 = time.perf_counter()
     for i, x in enumerate(clouds):
         a = time.perf_counter()
-        pts = torch.from_numpy(x).pin_memory().to(dev, non_blocking=True)
-        b = ph0.barcodes(pts, ws).raw.to("cpu")
+        b = plain_call(x)
         lat.append(time.perf_counter() - a)
-        if i % 97 == 0:
-            plain_bars[i] = b.numpy().tobytes()
+        plain_hash[i] = hashlib.blake2b(b.numpy().tobytes(), digest_size=16).digest()
     plain_s = time.perf_counter() - t0
     plain_rate = len(clouds) / plain_s
     out = {"clouds": len(clouds),
            "plain": {"clouds_per_s": plain_rate, "p50_ms": 1e3 * percentile(lat, 50),
-                     "p99_ms": 1e3 * percentile(lat, 99)}}
+                     "p99_ms": 1e3 * percentile(lat, 99),
+                     "note": "back-to-back calls: service time, no queueing"}}
+    # the plain calls under the same Poisson arrivals as the served form: one
+    # call at a time, each starting at its arrival or when the previous ends;
+    # latency = result on the host - arrival
+    for name, load in (("plain_load_0.9x", 0.9), ("plain_load_2x", 2.0)):
+        arr = inputs.poisson_arrivals(len(clouds), load * plain_rate)
+        lats, t0 = [], time.perf_counter()
+        for i, x in enumerate(clouds):
+            while time.perf_counter() - t0 < arr[i]:
+                pass
+            plain_call(x)
+            lats.append(time.perf_counter() - t0 - arr[i])
+        wall = time.perf_counter() - t0
+        out[name] = {"clouds_per_s": len(clouds) / (wall - arr[0]), "p50_ms": 1e3 * percentile(lats, 50),
+                     "p99_ms": 1e3 * percentile(lats, 99), "wall_s": wall}
     edges = sum(len(x) * (len(x) - 1) // 2 for x in clouds)
     out["edges"] = edges
     checked = 0
@@ -377,11 +430,14 @@ def run_serving(args, dev):
             bad = sum(f.status != 0 for f in done.values())
             out[name] = {"clouds_per_s": len(clouds) / (last - first), "p50_ms": 1e3 * percentile(lats, 50),
                          "p99_ms": 1e3 * percentile(lats, 99), "wall_s": wall, "errors": bad}
-            for i, want in plain_bars.items():
-                if done[i].bars.tobytes() != want:
+            for i, want in plain_hash.items():  # every served result against its plain call
+                got = hashlib.blake2b(done[i].bars.tobytes(), digest_size=16).digest()
+                if got != want or done[i].inf_vertex != 0:
                     raise RuntimeError(f"served cloud {i} differs from the plain call")
                 checked += 1
     out["bit_identical_to_plain_checked"] = checked
+    out["compare"] = ("plain_load_* and load_* share the arrival stream of each load; "
+                      "'saturated' queues every cloud at once")
     return out
 
 

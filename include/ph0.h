@@ -25,10 +25,14 @@
  *     bar that never dies sits on vertex 0.
  *
  * Memory: every pointer named *_dev is CUDA device memory (or managed memory)
- * owned by the caller; the library allocates nothing and keeps no global
- * state.  `ws` is a caller-owned device workspace of at least
- * ph0_workspace_bytes() bytes, 256-byte aligned; one workspace serves one call
- * in flight at a time.  `stream` is a cudaStream_t passed as void* (NULL =
+ * owned by the caller.  The workspace entry points allocate nothing: `ws` is
+ * a caller-owned device workspace of at least ph0_workspace_bytes() bytes,
+ * 256-byte aligned; one workspace serves one call in flight at a time.  The
+ * library keeps two kinds of state of its own: the 16 MiB device array of
+ * ph0_barcodes_noalloc() (one per GPU that loads the library, held until the
+ * process exits, plus a host-side cache of its device address), and the
+ * device arena and pinned pool a serving context (ph0_ctx_create) allocates
+ * and owns.  `stream` is a cudaStream_t passed as void* (NULL =
  * the legacy default stream).  All compute calls are asynchronous on
  * `stream`: they return host-detected errors immediately and leave
  * device-detected errors (non-finite input, a bounded wait that timed out) in
@@ -70,6 +74,17 @@ typedef struct {
     double death;      /* sqrt(death_sq), IEEE round to nearest                 */
 } ph0_bar;
 
+/* The bar that never dies (birth 0, death +inf): the class of the vertex
+ * that is the pivot row of no reduced column.  With the pivot convention
+ * above (largest row) this is always vertex 0; the kernels derive it from
+ * the pivot rows of the n-1 finite bars.  24 bytes. */
+typedef struct {
+    int32_t vertex;    /* representative vertex (the unpaired row)         */
+    int32_t _pad;
+    double birth;      /* 0                                                */
+    double death;      /* +inf                                             */
+} ph0_inf_bar;
+
 /* Counters of the last call on a workspace, read back by ph0_finish(). */
 typedef struct {
     int32_t status;          /* ph0_status of the device-side work            */
@@ -87,6 +102,10 @@ typedef struct {
     int64_t sorted_edges;    /* edges sorted: n(n-1)/2, or the prefix sorted by
                                 ph0_barcodes_early (n_distinct then counts the
                                 distinct values of that prefix)               */
+    int32_t inf_vertex;      /* vertex of the bar that never dies (0)         */
+    int32_t claim_rounds_max;/* most grid-wide claim rounds in one window     */
+    int64_t claim_attempts;  /* atomic claims issued in the reduction (two per
+                                candidate column and round)                   */
 } ph0_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -102,10 +121,13 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d);
 /* Whole path, steps 1-5 (Sec. 2; Sec. 4 steps 1-5).
  *   pts_dev   float32 [n, ld] row-major, the first d columns are used
  *   bars_dev  ph0_bar [n-1] output, in filtration order (increasing `order`)
- * The bar that never dies is (0, +inf) on vertex 0 and is not written.
+ *   inf_dev   ph0_inf_bar [1] output (device memory), the bar that never
+ *             dies: (0, +inf) on the vertex that is no pivot row; may be
+ *             NULL (ph0_finish() also reports the vertex)
  * Asynchronous; call ph0_finish() for the device status. */
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                 ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
+                 ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                 void *stream);
 
 /* Tuning of the kernels (chosen per dimension by the autotuner in the Python
  * package; a NULL pointer or a field set to -1 selects the built-in choice).
@@ -118,7 +140,11 @@ typedef struct {
                                128 (smaller when the tile would not fit shared memory)    */
     int32_t sort_top_bits;  /* width of the single top radix pass: 8 or 9 (a wider top
                                part takes two passes of 8); built-in 9                   */
-    int32_t reserved[5];
+    int32_t reduce_spin_limit; /* test aid: polls before a grid-barrier wait of the
+                               reduction gives up with PH0_ETIMEOUT (the kernel then
+                               returns and the workspace stays usable); -1 = built-in
+                               (2^24, about a second); 0 gives up at the first poll    */
+    int32_t reserved[4];
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits
@@ -137,12 +163,13 @@ typedef struct {
  * length in sorted_edges.  Fastest when the last killing edge comes early in
  * the edge order (clustered or uniform clouds). */
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                       ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream);
+                       ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                       void *stream);
 
 /* ph0_barcodes() with explicit tuning (NULL = built-in). */
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                       ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
-                       const ph0_tuning *tuning);
+                       ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                       void *stream, const ph0_tuning *tuning);
 
 /* Device time of each stage of one ph0_barcodes_profiled() call, from CUDA
  * events recorded on the caller's stream between the stages (milliseconds). */
@@ -161,8 +188,8 @@ typedef struct {
 /* ph0_barcodes() with a CUDA event between stages; waits for the stream and
  * fills `prof` (tracing aid: same kernels, same results). */
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                          ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
-                          const ph0_tuning *tuning, ph0_profile *prof);
+                          ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                          void *stream, const ph0_tuning *tuning, ph0_profile *prof);
 
 /* Waits for `stream`, then returns the device status of the last call made
  * with `ws` and, when stats != NULL, its counters. */
@@ -217,25 +244,30 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
 /* ---- allocation-free variant (the paper has no counterpart) ----
  *
  * ph0_barcodes() for callers that cannot allocate device memory where they
- * need barcodes: code running while a stream is captured, latency-critical
- * loops in which an allocation could synchronize the device or take a driver
- * lock, and hosts whose memory is all owned by their own pool.  Instead of a
- * caller workspace it uses a 16 MiB array in the library's device memory
- * (every GPU that loads the library holds it until the process exits); the
- * caller still passes the points and the bars buffer.  Clouds whose workspace
- * would exceed 16 MiB (ph0_workspace_bytes(n, d) > 16 MiB: n above 934 at
- * d = 3, above 928 at d = 32) are rejected with PH0_ETOOBIG before any work is queued.  It
- * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * need barcodes: latency-critical loops in which a cudaMalloc could
+ * synchronize the device or take a driver lock, and hosts (frameworks with
+ * their own caching allocator, embedded runtimes) whose device memory is all
+ * owned by their own pool, so that a raw allocation would fail or fragment
+ * it.  Instead of a caller workspace it uses a 16 MiB array in the library's
+ * device memory (every GPU that loads the library holds it until the
+ * process exits); the caller still passes the points and the outputs.
+ * Clouds whose workspace would exceed 16 MiB (ph0_workspace_bytes(n, d) >
+ * 16 MiB: n above 934 at d = 3, above 928 at d = 32) are rejected with
+ * PH0_ETOOBIG before any work is queued.  It allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call).
  *
- * The first call on a device looks up the device address of the array for
- * that device (with that device current); make that first call before any
- * stream capture.  All calls share the one array per device, which keeps the
- * last call's contents (every stage clears what it needs zeroed): calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialized by the caller.  Waits for `stream`, then returns the device
- * status of the call (as ph0_finish() would). */
+ * Synchronous: it waits for `stream` and reads the device status back
+ * before returning (as ph0_finish() would), so it cannot be recorded into a
+ * CUDA graph.  The first call on a device looks up the device address of the
+ * array for that device (with that device current) and keeps it for the rest
+ * of the process; after a cudaDeviceReset() of that device the kept address
+ * is stale, so this entry point must not be called again in that process.
+ * All calls share the one array per device, which keeps the last call's
+ * contents (every stage clears what it needs zeroed): calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialized by
+ * the caller. */
 int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                         ph0_bar *bars_dev, void *stream);
+                         ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *stream);
 
 /* ---- serving: a context that admits clouds as they arrive ----
  *
@@ -263,7 +295,7 @@ typedef struct {
     uint64_t tag;         /* as submitted                                           */
     int32_t status;       /* ph0_status of this cloud                               */
     int32_t n, d;
-    int32_t reserved;
+    int32_t inf_vertex;   /* vertex of the bar that never dies (0)                  */
     int64_t n_bars;       /* n - 1                                                  */
     const ph0_bar *bars;  /* host memory owned by the context until ph0_release     */
     double submit_time;   /* steady-clock seconds at ph0_submit                     */

@@ -43,6 +43,8 @@ class Stats(ctypes.Structure):
         ("candidates", ctypes.c_int64), ("rounds", ctypes.c_int64),
         ("n_bars", ctypes.c_int64), ("dist_tiles", ctypes.c_int64),
         ("dist_tiles_int", ctypes.c_int64), ("sorted_edges", ctypes.c_int64),
+        ("inf_vertex", ctypes.c_int32), ("claim_rounds_max", ctypes.c_int32),
+        ("claim_attempts", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -51,12 +53,14 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("dist_split16", ctypes.c_int32), ("dist_tile", ctypes.c_int32),
-                ("sort_top_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("sort_top_bits", ctypes.c_int32), ("reduce_spin_limit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
     @classmethod
-    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1):
+    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1):
         t = cls()
         t.dist_split16, t.dist_tile, t.sort_top_bits = dist_split16, dist_tile, sort_top_bits
+        t.reduce_spin_limit = reduce_spin_limit
         return t
 
     def as_dict(self):
@@ -85,10 +89,18 @@ class Options(ctypes.Structure):
     ]
 
 
+class InfBar(ctypes.Structure):
+    _fields_ = [("vertex", ctypes.c_int32), ("_pad", ctypes.c_int32),
+                ("birth", ctypes.c_double), ("death", ctypes.c_double)]
+
+
+INF_BAR_BYTES = ctypes.sizeof(InfBar)  # 24
+
+
 class Result(ctypes.Structure):
     _fields_ = [
         ("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_int32),
-        ("d", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_bars", ctypes.c_int64),
+        ("d", ctypes.c_int32), ("inf_vertex", ctypes.c_int32), ("n_bars", ctypes.c_int64),
         ("bars", ctypes.c_void_p), ("submit_time", ctypes.c_double),
         ("done_time", ctypes.c_double),
     ]
@@ -104,15 +116,15 @@ SIGNATURES = {
     "ph0_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ph0_abi_version": (ctypes.c_int32, []),
     "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
-    "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
-    "ph0_barcodes_early": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP]),
+    "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
+    "ph0_barcodes_early": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
-    "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
+    "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
                                           ctypes.POINTER(Tuning)]),
-    "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP,
+    "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
                                              ctypes.POINTER(Tuning), ctypes.POINTER(Profile)]),
     "ph0_trace_windows": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32]),
-    "ph0_barcodes_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP]),
+    "ph0_barcodes_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP]),
     "ph0_distances": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_ctx_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.POINTER(_VP)]),
     "ph0_submit": (ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.c_uint64]),

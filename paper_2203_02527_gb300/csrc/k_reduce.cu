@@ -67,6 +67,11 @@ __global__ void k_reduce_init(ReduceArgs A) {
         A.kill_val[v] = 0;
     }
     if (tid == 0) {
+        // XOR of 0..n-1; k_emit folds in every pivot row, leaving the vertex
+        // that is no pivot row: the bar that never dies
+        const uint64_t top = A.n > 0 ? uint64_t(A.n - 1) : 0;
+        const uint32_t x = (top & 3) == 0 ? uint32_t(top) : (top & 3) == 1 ? 1u : (top & 3) == 2 ? uint32_t(top + 1) : 0u;
+        A.h->inf_xor = x;
         A.h->npiv = 0;
         A.h->nlist[0] = 0;
         A.h->nlist[1] = 0;
@@ -76,9 +81,9 @@ __global__ void k_reduce_init(ReduceArgs A) {
     }
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
-// the CTA) if the kernel must stop.
-__device__ bool grid_barrier(Header *h, int *s_ok) {
+// Grid-wide barrier with a bounded wait (spin_limit polls).  Returns false
+// (in every thread of the CTA) if the kernel must stop.
+__device__ bool grid_barrier(Header *h, int *s_ok, uint32_t spin_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -94,7 +99,7 @@ __device__ bool grid_barrier(Header *h, int *s_ok) {
             uint32_t spins = 0;
             while (ld_volatile(&h->bar_gen) == gen) {
                 if (ld_volatile(&h->abort)) { ok = 0; break; }
-                if (++spins > kSpinLimit) {
+                if (++spins > spin_limit) {
                     set_status(h, PH0_ETIMEOUT);
                     atomicExch(&h->abort, 1);
                     ok = 0;
@@ -161,7 +166,7 @@ __device__ __forceinline__ uint16_t local_find(uint16_t *par, uint16_t x) {
 // __syncthreads instead of grid barriers.  Returns the number of rounds.
 __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *val,
                                 const uint32_t *list, uint32_t ncur, uint16_t *s_comp,
-                                unsigned char *s_tail, uint32_t target) {
+                                unsigned char *s_tail, uint32_t target, uint32_t &claims) {
     constexpr int C = kTailCap;
     uint32_t *s_p = reinterpret_cast<uint32_t *>(s_tail);        // [C] position
     uint32_t *s_lres = s_p + C;                                   // [2C] claim per local root
@@ -229,6 +234,7 @@ __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *
             s_rb[i] = b;
             atomicMin(s_lres + a, s_p[i]);
             atomicMin(s_lres + b, s_p[i]);
+            claims += 2;
         }
         __syncthreads();
         uint32_t left = 0;
@@ -291,6 +297,8 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     int64_t tail_total = 0;   // shared-memory rounds (CTA 0)
     int windows = 0;
     int64_t candidates = 0;
+    uint32_t claims = 0;          // atomic claims issued by this thread
+    uint32_t rounds_max = 0;      // most claim rounds in one window (CTA 0)
     for (;;) {
         const uint32_t npiv = __ldcg(&h->npiv);
         if (pos0 >= m || npiv >= target) break;
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             const bool has = s_hkey[slot] != kEmpty;
             warp_append(has, s_hval[slot], A.cand0, &h->nlist[0]);
         }
-        if (!grid_barrier(h, &s_ok)) return;
+        if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
 
         // ---------------- R: claim pivots in rounds ------------------------
         int cur = 0;
@@ -428,9 +436,10 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                     A.candr[i] = (ru << 16) | rv;
                     atomicMin(A.res + ru, tag | p);
                     atomicMin(A.res + rv, tag | p);
+                    claims += 2;
                 }
             }
-            if (!grid_barrier(h, &s_ok)) return;
+            if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
             // commit the columns that hold their larger root H: pivot H
             for (int64_t b = int64_t(blockIdx.x) * kReduceThreads; b < ncur; b += gstride) {
                 const int64_t i = b + tid;
@@ -452,7 +461,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 }
                 warp_append(keep, p, next, next_count);
             }
-            if (!grid_barrier(h, &s_ok)) return;
+            if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
             cur ^= 1;
             ncur = __ldcg(&h->nlist[cur]);
         }
@@ -462,8 +471,8 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             if (blockIdx.x == 0)
                 tail_total += tail_rounds(A, h, val, cur ? A.cand1 : A.cand0, ncur, s_comp,
                                           reinterpret_cast<unsigned char *>(s_comp + ((n + 7) & ~int64_t(7))),
-                                          target);
-            if (!grid_barrier(h, &s_ok)) return;
+                                          target, claims);
+            if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
         }
 
         if (tr) rec[9] = gtimer();
@@ -471,8 +480,12 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         for (int64_t v = gtid; v < n; v += gstride)
             A.comp[v] = find_root(A.parent, __ldcg(A.comp + v));
         if (blockIdx.x == 0 && tid == 0) h->nlist[0] = 0;
-        if (!grid_barrier(h, &s_ok)) return;
+        if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
 
+        {
+            const uint32_t wr = (round - round_before) + uint32_t(tail_total - tail_before);
+            rounds_max = wr > rounds_max ? wr : rounds_max;
+        }
         if (tr) {
             rec[3] = round - round_before;
             rec[4] = uint64_t(tail_total - tail_before);
@@ -485,12 +498,15 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         else if (nwin * 2 < W) W *= 2;
         if (W > kMaxWindow) W = kMaxWindow;
     }
+    claims = __reduce_add_sync(0xffffffffu, claims);
+    if ((tid & 31) == 0 && claims) atomicAdd(&h->claim_attempts, (unsigned long long)claims);
     if (blockIdx.x == 0 && tid == 0) {
         h->windows = windows;
         h->edges_scanned = pos0;
         h->candidates = candidates;
         h->rounds = int64_t(round) + tail_total;
         h->n_bars = __ldcg(&h->npiv);
+        atomicMax(&h->claim_rounds_max, rounds_max);
     }
 }
 
@@ -533,6 +549,7 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
         aval = cpref[c0 / kDedupeChunk] + __reduce_add_sync(0xffffffffu, cnt);
     }
     if (lane != 0) return;
+    atomicXor(&h->inf_xor, low);
     const uint32_t vv = sodd ? val1[p] : val0[p];
     const uint64_t key = keys[p];
     ph0_bar b;
@@ -546,8 +563,34 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
     bars[j] = b;
 }
 
+// The bar that never dies: the vertex left in inf_xor once k_emit has folded
+// in the n-1 pivot rows (every vertex but one is the pivot row of exactly one
+// reduced column).  n = 1: vertex 0.
+__global__ void k_inf(Header *h, int64_t n, ph0_inf_bar *inf) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t v = n > 1 ? ld_volatile(&h->inf_xor) : 0u;
+    if (int64_t(v) >= n) {  // only after a reported error (fewer than n-1 bars)
+        set_status(h, PH0_EINTERNAL);
+        v = 0;
+    }
+    h->inf_vertex = int32_t(v);
+    if (inf) {
+        ph0_inf_bar b;
+        b.vertex = int32_t(v);
+        b._pad = 0;
+        b.birth = 0.0;
+        b.death = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+        *inf = b;
+    }
+}
+
 // ------------------------------------------------------------------ host ---
 int sm_count();
+
+cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s) {
+    k_inf<<<1, 32, 0, s>>>(h, n, inf);
+    return cudaGetLastError();
+}
 
 // Snapshot labels (2 B per vertex, rounded up to 16 B) plus the tail arrays.
 size_t reduce_dyn_smem(int64_t n) {

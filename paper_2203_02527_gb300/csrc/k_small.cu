@@ -256,8 +256,16 @@ __device__ void small_cloud(const SmallTask &T, SmallSmem &S) {
         b.death = __dsqrt_rn(b.death_sq);
         T.bars[rank] = b;
     }
-    if (tid == 0)
-        *T.status = S.bad ? PH0_ENONFINITE : (nb == n - 1 ? PH0_OK : PH0_EINTERNAL);
+    if (tid == 0) {
+        // the bar that never dies: the vertex that is no pivot row (XOR of
+        // 0..n-1 and of the n-1 pivot rows)
+        uint32_t x = 0;
+        for (int w = 0; w < n; ++w) x ^= uint32_t(w);
+        for (int j = 0; j < nb; ++j) x ^= S.klow[j];
+        const bool ok = nb == n - 1 && x < uint32_t(n);
+        T.status[1] = ok ? int32_t(x) : 0;
+        T.status[0] = S.bad ? PH0_ENONFINITE : (ok ? PH0_OK : PH0_EINTERNAL);
+    }
     __syncthreads();
 }
 
@@ -273,7 +281,10 @@ k_small(const SmallTask *__restrict__ tasks, const int32_t *__restrict__ ntasks,
         if (t >= uint32_t(*ntasks)) break;
         const SmallTask task = tasks[t];
         if (task.n < 2) {
-            if (threadIdx.x == 0) *task.status = PH0_OK;
+            if (threadIdx.x == 0) {
+                task.status[0] = PH0_OK;
+                task.status[1] = 0;
+            }
             continue;
         }
         small_cloud(task, S);

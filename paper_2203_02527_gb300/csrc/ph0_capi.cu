@@ -1,9 +1,12 @@
 // ph0_capi.cu -- the C ABI of libph0 (declared in include/ph0.h): argument
 // checks, workspace carving and kernel launches for the five steps of the
-// barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).  No device allocation, no
-// global state: every buffer is caller-owned and every call is asynchronous
-// on the caller's stream, except ph0_barcodes_early (which waits to decide how
-// much of the edge order to sort) and ph0_barcodes_noalloc.
+// barcode path (Rawson, Sec. 2; Sec. 4 steps 1-5).  The workspace entry
+// points allocate nothing: every buffer is caller-owned and every call is
+// asynchronous on the caller's stream, except ph0_barcodes_early (which waits
+// to decide how much of the edge order to sort).  The one piece of global
+// state, and the one buffer the caller does not own, is the fixed device
+// array of ph0_barcodes_noalloc (end of this file) with its per-device
+// address cache; that entry point is synchronous.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -50,6 +53,7 @@ cudaError_t launch_backward(const float *pts, int64_t n, int32_t d, int64_t ld, 
                             int64_t nb, const double *dl, float *grad, double *acc, cudaStream_t s);
 
 cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s);
+cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s);
 cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
@@ -78,11 +82,14 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? PH0_OK : PH0_ECUDA; }
 // Tuning with the built-in choices filled in.
 struct Tune {
     int split16 = kDefaultDistSplit16, tile = -1, top_bits = kDefaultTopBits;
+    uint32_t spin_limit = kSpinLimit;
     explicit Tune(const ph0_tuning *t) {
         if (!t) return;
         if (t->dist_split16 >= 0 && t->dist_split16 <= 16) split16 = t->dist_split16;
         if (t->dist_tile == 32 || t->dist_tile == 64 || t->dist_tile == 128) tile = t->dist_tile;
         if (t->sort_top_bits == 8 || t->sort_top_bits == 9) top_bits = t->sort_top_bits;
+        if (t->reduce_spin_limit >= 0 && uint32_t(t->reduce_spin_limit) < kSpinLimit)
+            spin_limit = uint32_t(t->reduce_spin_limit);
     }
 };
 
@@ -138,7 +145,8 @@ cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, i
 // the pivot claiming.  val is the workspace's ping-pong buffer (sort_h != null
 // selects the one holding the sorted data) or the caller's.
 cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
-                       const uint32_t *val1, const Header *sort_h, cudaStream_t s) {
+                       const uint32_t *val1, const Header *sort_h, cudaStream_t s,
+                       uint32_t spin_limit = kSpinLimit) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -157,20 +165,22 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
     A.trace = at<uint64_t>(ws, L.trace);
     int64_t w0 = 2 * n > 4096 ? 2 * n : 4096;
     A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
+    A.spin_limit = spin_limit;
     return launch_reduce(A, s);
 }
 
 // The read-out after run_reduce: order the n-1 pivot columns by position
 // (their discovery order within a window is not the filtration order) and
-// emit the bars.  key as val; a is the caller's per-edge index, or null with
-// cpref the workspace's chunk prefixes of the count-mode scan.
+// emit the bars, then the bar that never dies (inf may be null).  key as val;
+// a is the caller's per-edge index, or null with cpref the workspace's chunk
+// prefixes of the count-mode scan.
 cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
-                           ph0_bar *bars, cudaStream_t s) {
+                           ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t nb = n - 1;
-    if (nb <= 0) return cudaSuccess;
+    if (nb <= 0) return launch_inf(h, n, inf, s);
     Header *kh = at<Header>(ws, L.aux_hdr);
     cudaError_t e = cudaMemsetAsync(kh, 0, kHeaderBytes, s);
     if (e != cudaSuccess) return e;
@@ -184,24 +194,27 @@ cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, cons
     e = launch_sort_passes(kk0, kk1, kv0, kv1, nb, at<uint64_t>(ws, L.kill_look[0]),
                            at<uint64_t>(ws, L.kill_look[1]), kh, s);
     if (e != cudaSuccess) return e;
-    return launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
-                       reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
-                       key0, key1, sort_h, a, cpref, bars, s);
+    e = launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
+                    reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
+                    key0, key1, sort_h, a, cpref, bars, s);
+    if (e != cudaSuccess) return e;
+    return launch_inf(h, n, inf, s);
 }
 
 // Steps 4-5 plus the read-out on all m = n(n-1)/2 sorted edges.
 cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
                             const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                             const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
-                            ph0_bar *bars, cudaStream_t s, cudaEvent_t after_reduce = nullptr) {
+                            ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s,
+                            cudaEvent_t after_reduce = nullptr, uint32_t spin_limit = kSpinLimit) {
     const int64_t m = n_edges(n);
-    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s);
+    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit);
     if (e != cudaSuccess) return e;
     if (after_reduce) {
         e = cudaEventRecord(after_reduce, s);
         if (e != cudaSuccess) return e;
     }
-    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, s);
+    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s);
 }
 
 }  // namespace
@@ -226,7 +239,7 @@ const char *ph0_strerror(int status) {
     }
 }
 
-int32_t ph0_abi_version(void) { return 2; }
+int32_t ph0_abi_version(void) { return 3; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
     if (check_sizes(n, d, d) != PH0_OK) return 0;
@@ -234,11 +247,13 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d) {
 }
 
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
-                       void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning) {
+                       ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream,
+                       const ph0_tuning *tuning) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
-    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
+        return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
     const Tune t(tuning);
@@ -251,26 +266,29 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
+    if (e == cudaSuccess)
+        e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, nullptr,
+                            t.spin_limit);
     return cuda_status(e);
 }
 
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
-                 void *ws, size_t ws_bytes, void *stream) {
-    return ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, ws, ws_bytes, stream, nullptr);
+                 ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
+    return ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
 }
 
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
-                       void *ws, size_t ws_bytes, void *stream) {
+                       ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
-    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
+        return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto whole = [&]() {  // the whole path, then its device status
-        const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, ws, ws_bytes, stream, nullptr);
+        const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
         return r != PH0_OK ? r : ph0_finish(ws, stream, nullptr);
     };
     if (n < 3) return whole();
@@ -398,7 +416,8 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
 
     // step 3 on the prefix (count mode) and the read-out; then the prefix length
     e = launch_dedupe(k0, k0, nullptr, P, nullptr, cpref, dlook, h, s);
-    if (e == cudaSuccess) e = order_and_emit(ws, L, n, P, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, s);
+    if (e == cudaSuccess)
+        e = order_and_emit(ws, L, n, P, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, inf_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h->sorted_edges, &P, sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return PH0_ECUDA;
@@ -406,12 +425,13 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
 }
 
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                          ph0_bar *bars_dev, void *ws, size_t ws_bytes, void *stream,
-                          const ph0_tuning *tuning, ph0_profile *prof) {
+                          ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                          void *stream, const ph0_tuning *tuning, ph0_profile *prof) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || !prof || (n > 1 && !bars_dev)) return PH0_EINVAL;
-    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
+        return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -449,7 +469,9 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 + kMaxPasses], s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s, ev[4 + kMaxPasses]);
+    if (e == cudaSuccess)
+        e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, ev[4 + kMaxPasses],
+                            t.spin_limit);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5 + kMaxPasses], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[5 + kMaxPasses]);
     if (e == cudaSuccess) {
@@ -493,6 +515,9 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
         stats->dist_tiles = int64_t(hh.dist_tiles);
         stats->dist_tiles_int = int64_t(hh.dist_tiles_exact_int);
         stats->sorted_edges = hh.sorted_edges;
+        stats->inf_vertex = hh.inf_vertex;
+        stats->claim_rounds_max = int32_t(hh.claim_rounds_max);
+        stats->claim_attempts = int64_t(hh.claim_attempts);
     }
     return hh.status;
 }
@@ -581,7 +606,7 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev, const uint32_t *a_dev,
     cudaError_t e = cudaMemsetAsync(at<Header>(ws, L.hdr), 0, kHeaderBytes, s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, val_sorted_dev, val_sorted_dev, key_sorted_dev, key_sorted_dev,
-                            nullptr, a_dev, nullptr, bars_dev, s);
+                            nullptr, a_dev, nullptr, bars_dev, nullptr, s);
     return cuda_status(e);
 }
 
@@ -605,18 +630,21 @@ int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d, int64_t ld
 
 // ---------------------------------------------------------------------------
 // Allocation-free entry point.  Some callers cannot call cudaMalloc (or any
-// allocator) at the point where they need barcodes: code that runs while a
-// stream is being captured, latency-critical loops where an allocation could
-// synchronize the device or take a driver lock, and hosts that own all device
-// memory through their own pool and forbid raw allocations.  For clouds small
-// enough to fit, this entry point takes its workspace from a fixed array in
-// the library's device memory instead of from the caller.
+// allocator) at the point where they need barcodes: latency-critical loops
+// where an allocation could synchronize the device or take a driver lock,
+// and hosts that own all device memory through their own pool and forbid
+// raw allocations.  For clouds small enough to fit, this entry point takes
+// its workspace from a fixed array in the library's device memory instead of
+// from the caller.  It waits for its stream before returning, so it is not
+// meant for stream capture.
 // ---------------------------------------------------------------------------
 namespace ph0 {
 namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB, held by every GPU that loads the library
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
+// Device address of the array per device, looked up once per device and
+// process; a cudaDeviceReset() of the device makes it stale.
 void *g_noalloc_addr[kNoAllocMaxDevices] = {};
 }  // namespace
 }  // namespace ph0
@@ -624,11 +652,11 @@ void *g_noalloc_addr[kNoAllocMaxDevices] = {};
 static __device__ __align__(256) unsigned char g_noalloc_scratch[ph0::kNoAllocScratchBytes];
 
 extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
-                                    ph0_bar *bars_dev, void *stream) {
+                                    ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *stream) {
     int rc = check_sizes(n, d, ld);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || (n > 1 && !bars_dev)) return PH0_EINVAL;
-    if (!aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    if (!aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8)) return PH0_EINVAL;
     const Layout L(n, d);
     if (L.total > kNoAllocScratchBytes) return PH0_ETOOBIG;
     int dev = 0;
@@ -659,9 +687,11 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
-    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s);
+    // the status word is read on the caller's stream (a plain copy would go
+    // through the legacy default stream and wait for other blocking streams)
     int32_t status = PH0_OK;
-    if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? status : PH0_ECUDA;
 }

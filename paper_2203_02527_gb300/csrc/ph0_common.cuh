@@ -63,9 +63,11 @@ __host__ __device__ __forceinline__ int prefix_shift(uint64_t kmin, uint64_t kma
 // Lives at offset 0 of the workspace.  Every counter the kernels share.
 struct Header {
     int32_t status;              // ph0_status, first device error wins
+    int32_t inf_vertex;          // vertex of the bar that never dies (read with status)
     int32_t sort_passes;
     int32_t key_bits;
     int32_t windows;
+    uint32_t inf_xor;            // XOR of 0..n-1 and of every pivot row emitted
     uint64_t kmin;               // min / max key over the keys being sorted
     uint64_t kmax;
     int64_t n_distinct;
@@ -87,6 +89,9 @@ struct Header {
     uint32_t defer_count;        // groups the fix-up left to its second kernel
     uint32_t pad[1];
     int64_t sorted_edges;        // edges sorted: m, or the prefix of the early path
+    unsigned long long claim_attempts;  // atomic claims of the reduction (grid and tail rounds)
+    uint32_t claim_rounds_max;   // most claim rounds in one window
+    uint32_t pad2;
     // class partition of the early path (radix slot kClassSlot): the key
     // bins of its histogram and the classes' bin ranges [bound[c], bound[c+1])
     uint64_t part_kmin;
@@ -191,6 +196,7 @@ struct ReduceArgs {
     Header *h;
     int64_t w0;                    // first window size
     uint64_t *trace;               // [kTraceWindows][kTraceWords]
+    uint32_t spin_limit;           // polls before a grid-barrier wait gives up
 };
 
 // One cloud of a fused small-cloud batch (k_small.cu).
@@ -198,7 +204,7 @@ struct SmallTask {
     const float *pts;      // device [n, ld]
     int64_t *fixed;        // device scratch [n * d] int64 (fixed-point coordinates)
     ph0_bar *bars;         // device [n - 1]
-    int32_t *status;       // device, one word per task
+    int32_t *status;       // device, two words per task: status, vertex of the infinite bar
     int32_t n, d, ld, pad;
 };
 

@@ -87,6 +87,7 @@ struct Request {
     uint64_t tag = 0;
     int32_t n = 0, d = 0;
     int32_t status = PH0_OK;
+    int32_t inf_vertex = 0;
     bool small = false;
     // pinned host: [points | bars | status word]
     size_t h_off = 0, h_bytes = 0;
@@ -154,6 +155,13 @@ struct ph0_ctx {
         return pts + bars + work + 256;
     }
 
+    // a request whose device work finished: its status and the vertex of its
+    // infinite bar, both written by the device into the pinned pool
+    void complete_ok(Request *r) {
+        r->inf_vertex = status_host(r)[1];
+        complete(r, status_host(r)[0]);
+    }
+
     void complete(Request *r, int32_t status) {
         r->status = status;
         r->t_done = now_s();
@@ -171,12 +179,13 @@ struct ph0_ctx {
                    align_up(size_t(r->n > 1 ? r->n - 1 : 1) * sizeof(ph0_bar), 256);
         cudaError_t e = cudaMemcpyAsync(d_pts, pts_host(r), size_t(r->n) * r->d * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return e;
-        const int rc = ph0_barcodes(d_pts, r->n, r->d, r->d, d_bars, ws, r->ws_bytes, s);
+        const int rc = ph0_barcodes(d_pts, r->n, r->d, r->d, d_bars, nullptr, ws, r->ws_bytes, s);
         if (rc != PH0_OK) return cudaErrorUnknown;
         if (r->n > 1)
             e = cudaMemcpyAsync(bars_host(r), d_bars, size_t(r->n - 1) * sizeof(ph0_bar), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(status_host(r), ws, sizeof(int32_t), cudaMemcpyDeviceToHost, s);  // header status
+            e = cudaMemcpyAsync(status_host(r), ws, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                s);  // header: status, vertex of the infinite bar
         if (e == cudaSuccess) e = cudaEventRecord(events[k], s);
         return e;
     }
@@ -211,7 +220,7 @@ struct ph0_ctx {
                 e = cudaMemcpyAsync(bars_host(r), h_tasks[i].bars, size_t(r->n - 1) * sizeof(ph0_bar),
                                     cudaMemcpyDeviceToHost, small_stream);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(status_host(r), h_tasks[i].status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                e = cudaMemcpyAsync(status_host(r), h_tasks[i].status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                     small_stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(small_event, small_stream);
@@ -230,7 +239,8 @@ struct ph0_ctx {
                 busy = true;
                 const cudaError_t q = cudaEventQuery(events[k]);
                 if (q == cudaErrorNotReady) continue;
-                complete(r, q == cudaSuccess ? *status_host(r) : PH0_ECUDA);
+                if (q == cudaSuccess) complete_ok(r);
+                else complete(r, PH0_ECUDA);
                 slot_req[k] = nullptr;
                 cv_done.notify_all();
             }
@@ -238,7 +248,10 @@ struct ph0_ctx {
                 busy = true;
                 const cudaError_t q = cudaEventQuery(small_event);
                 if (q != cudaErrorNotReady) {
-                    for (Request *r : small_batch) complete(r, q == cudaSuccess ? *status_host(r) : PH0_ECUDA);
+                    for (Request *r : small_batch) {
+                        if (q == cudaSuccess) complete_ok(r);
+                        else complete(r, PH0_ECUDA);
+                    }
                     small_batch.clear();
                     cv_done.notify_all();
                 }
@@ -344,6 +357,7 @@ int ph0_ctx_create(const ph0_options *opt, ph0_ctx **out) {
     }
     if (e != cudaSuccess) {
         ph0_ctx_destroy(c);
+        cudaGetLastError();  // a failed allocation is not sticky: clear it for the caller's next check
         return PH0_ECUDA;
     }
     c->worker = std::thread([c] { c->run(); });
@@ -402,6 +416,7 @@ int ph0_poll(ph0_ctx *c, ph0_result *out, int32_t max, int32_t *got, int32_t wai
         o.status = r->status;
         o.n = r->n;
         o.d = r->d;
+        o.inf_vertex = r->inf_vertex;
         o.n_bars = r->n - 1;
         o.bars = c->bars_host(r);
         o.submit_time = r->t_submit;

@@ -60,6 +60,18 @@ def noisy_circles(n_per: int, n_circles: int, d: int, noise: float = 0.02,
     return np.concatenate(out, axis=0).astype(np.float32)
 
 
+def circles_with_outliers(n_per: int, n_circles: int, d: int, n_out: int,
+                          far: float = 60.0, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """noisy_circles(n_per, n_circles, d) followed by n_out outliers at
+    far * e_i (i = 0..n_out-1, n_out <= d): every edge from an outlier is
+    longer than every edge among the circles, so the last edges to join a
+    class come at the end of the edge order."""
+    pts = noisy_circles(n_per, n_circles, d, seed=seed).astype(np.float64)
+    out = np.zeros((n_out, d))
+    out[np.arange(n_out), np.arange(n_out)] = far
+    return np.concatenate([pts, out]).astype(np.float32)
+
+
 # ---------------------------------------------------------------------------
 # Named workloads (sizes and distributions of the benchmark configurations)
 # ---------------------------------------------------------------------------

@@ -4,8 +4,7 @@ come from PyTorch; all computation is in libph0's CUDA kernels.
     bars = barcodes(points)          # points: float32 [N, d] CUDA tensor
     bars.death, bars.u, bars.v ...   # CUDA tensors, filtration order
     bars.numpy()                     # structured array (host copy)
-
-The bar that never dies is (0, +inf) on vertex 0 (not stored).
+    bars.inf                         # the bar that never dies: (vertex, 0.0, inf)
 """
 from __future__ import annotations
 
@@ -69,6 +68,7 @@ class Bars:
     raw: torch.Tensor          # uint8 [n-1, 40] device buffer
     n: int
     stats: dict | None = None
+    inf_raw: torch.Tensor | None = None   # uint8 [24] device buffer (ph0_inf_bar)
 
     def __getattr__(self, name):
         if name in _FIELDS:
@@ -80,7 +80,19 @@ class Bars:
     def numpy(self) -> np.ndarray:
         return self.raw.cpu().numpy().reshape(-1).view(BAR_DTYPE).copy()
 
-    inf_vertex = 0
+    @property
+    def inf(self) -> tuple:
+        """The bar that never dies, as written by the kernels: (vertex, birth, death)."""
+        b = _lib.InfBar.from_buffer_copy(self.inf_raw.cpu().numpy().tobytes())
+        return int(b.vertex), float(b.birth), float(b.death)
+
+    @property
+    def inf_vertex(self) -> int:
+        return self.inf[0]
+
+
+def _inf_buffer(device) -> torch.Tensor:
+    return torch.empty(_lib.INF_BAR_BYTES, dtype=torch.uint8, device=device)
 
 
 def _points(pts: torch.Tensor):
@@ -109,15 +121,16 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     pts, n, d, ld = _points(pts)
     ws = ws or _workspace(n, d, pts.device)
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
+    inf = _inf_buffer(pts.device)
     s = _stream()
     lib = _lib.load()
     t = _tuning(n, d, tuning)
-    check(lib.ph0_barcodes_tuned(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, s,
+    check(lib.ph0_barcodes_tuned(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes, s,
                                  ctypes.byref(t) if t is not None else None), "ph0_barcodes")
     st = None
     if sync or stats:
         st = finish(ws)
-    return Bars(bars, n, st)
+    return Bars(bars, n, st, inf)
 
 
 def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None) -> Bars:
@@ -127,9 +140,10 @@ def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None) -> Bars:
     pts, n, d, ld = _points(pts)
     ws = ws or _workspace(n, d, pts.device)
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
-    check(_lib.load().ph0_barcodes_early(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes, _stream()),
-          "ph0_barcodes_early")
-    return Bars(bars, n, finish(ws))
+    inf = _inf_buffer(pts.device)
+    check(_lib.load().ph0_barcodes_early(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
+                                         _stream()), "ph0_barcodes_early")
+    return Bars(bars, n, finish(ws), inf)
 
 
 def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None,
@@ -141,11 +155,12 @@ def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torc
     if bars is None:
         bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     prof = _lib.Profile()
+    inf = _inf_buffer(pts.device)
     t = _tuning(n, d, tuning)
-    check(_lib.load().ph0_barcodes_profiled(_ptr(pts), n, d, ld, _ptr(bars), ws.ptr, ws.nbytes,
+    check(_lib.load().ph0_barcodes_profiled(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
                                             _stream(), ctypes.byref(t) if t is not None else None,
                                             ctypes.byref(prof)), "ph0_barcodes_profiled")
-    return Bars(bars, n, None), prof.as_dict()
+    return Bars(bars, n, None, inf), prof.as_dict()
 
 
 def trace_windows(ws: Workspace, n: int, d: int, max_windows: int = 256):

@@ -32,6 +32,7 @@ class Finished:
     bars: np.ndarray
     submit_time: float
     done_time: float
+    inf_vertex: int = 0        # vertex of the bar that never dies
 
     @property
     def latency(self) -> float:
@@ -74,7 +75,7 @@ class Server:
             else:
                 bars = np.zeros(0, BAR_DTYPE)
             out.append(Finished(int(r.tag), int(r.status), int(r.n), int(r.d), bars,
-                                float(r.submit_time), float(r.done_time)))
+                                float(r.submit_time), float(r.done_time), int(r.inf_vertex)))
             if release:
                 check(self._lib.ph0_release(self._h, r.tag), "ph0_release")
         return out

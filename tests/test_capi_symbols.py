@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     # host-only calls work without a device
     lib2 = _lib.load()
-    assert lib2.ph0_abi_version() == 2
+    assert lib2.ph0_abi_version() == 3
     assert lib2.ph0_strerror(0) == b"ok"
     assert lib2.ph0_workspace_bytes(0, 3) == 0
     assert lib2.ph0_workspace_bytes(256, 3) > 256 * 255 // 2 * 12
@@ -59,3 +59,30 @@ def test_library_leaves_none_of_its_own_symbols_unresolved():
     out = subprocess.run([nm, "-D", "--undefined-only", path], capture_output=True, text=True).stdout
     own = [line for line in out.splitlines() if "ph0" in line]
     assert not own, own
+
+
+def test_bad_input_is_rejected_on_the_host_before_any_cuda_call():
+    """Host-side checks of every whole-path entry point: each error below is
+    returned before the library touches CUDA, so this runs without a GPU
+    (the pointers are never dereferenced)."""
+    from paper_2203_02527_gb300 import _lib
+    lib = _lib.load()
+    vp = ctypes.c_void_p
+    pts, bars, inf, ws = vp(0x10000), vp(0x20000), vp(0x30000), vp(0x40000)
+    need = lib.ph0_workspace_bytes(10, 3)
+    for name in ("ph0_barcodes", "ph0_barcodes_early"):
+        f = getattr(lib, name)
+        assert f(pts, 10, 3, 2, bars, inf, ws, need, None) == 1          # ld < d
+        assert f(pts, 0, 3, 3, bars, inf, ws, need, None) == 1           # n < 1
+        assert f(pts, 10, 0, 3, bars, inf, ws, need, None) == 1          # d < 1
+        assert f(pts, 65536, 3, 3, bars, inf, ws, need, None) == 3       # n > 65535
+        assert f(pts, 10, 1025, 1025, bars, inf, ws, need, None) == 3    # d > 1024
+        assert f(None, 10, 3, 3, bars, inf, ws, need, None) == 1         # no points
+        assert f(pts, 10, 3, 3, None, inf, ws, need, None) == 1          # no bars buffer
+        assert f(pts, 10, 3, 3, bars, inf, vp(0x40008), need, None) == 1  # workspace not 256-aligned
+        assert f(pts, 10, 3, 3, bars, vp(0x30004), ws, need, None) == 1  # inf bar not 8-aligned
+        assert f(pts, 10, 3, 3, bars, inf, ws, need - 1, None) == 4      # workspace too small
+    assert lib.ph0_barcodes_noalloc(pts, 2000, 3, 3, bars, inf, None) == 3  # beyond its array
+    assert lib.ph0_barcodes_noalloc(pts, 10, 3, 2, bars, inf, None) == 1
+    assert lib.ph0_sort(None, None, -1, ws, need, None) == 1
+    assert lib.ph0_dedupe(None, 2 ** 31, None, ws, need, None) == 1

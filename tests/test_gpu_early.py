@@ -28,17 +28,20 @@ def _cuda(x):
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_early_matches_oracle(case):
     x = CASES[case]()
-    want, _, _ = oracle.barcodes(x)
+    want, inf_v, _ = oracle.barcodes(x)
     got = _ph0().barcodes_early(_cuda(x))
     assert_bars_equal(got.numpy(), want)
     assert got.stats["status"] == 0 and got.stats["n_bars"] == len(x) - 1
+    assert got.inf == (inf_v, 0.0, float("inf"))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 31, 33, 129, 257, 1000])
 def test_early_small_and_ragged(n):
     x = inputs.uniform(n, 3, seed=500 + n)
-    want, _, _ = oracle.barcodes(x)
-    assert_bars_equal(_ph0().barcodes_early(_cuda(x)).numpy(), want)
+    want, inf_v, _ = oracle.barcodes(x)
+    got = _ph0().barcodes_early(_cuda(x))
+    assert_bars_equal(got.numpy(), want)
+    assert got.inf == (inf_v, 0.0, float("inf"))
 
 
 def test_early_sorts_a_short_prefix_of_a_uniform_cloud():

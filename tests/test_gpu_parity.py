@@ -77,11 +77,13 @@ def test_steps_bit_exact(case):
     # steps 4-5
     bars = ph0.reduce(n, val, a, key)
     assert_bars_equal(bars.numpy(), ref["bars"])
-    # the whole path in one call
+    # the whole path in one call, with the bar that never dies
     whole = ph0.barcodes(pts)
     assert_bars_equal(whole.numpy(), ref["bars"])
     assert whole.stats["n_distinct"] == ref["n_distinct"]
     assert whole.stats["n_bars"] == n - 1
+    assert whole.inf == (ref["inf_vertex"], 0.0, float("inf"))
+    assert whole.stats["inf_vertex"] == ref["inf_vertex"]
 
 
 @pytest.mark.parametrize("name", sorted(golden.FIXTURES))
@@ -104,6 +106,7 @@ def test_small_and_ragged_sizes(n):
     got = ph0.barcodes(_cuda(x))
     assert_bars_equal(got.numpy(), want)
     assert inf_v == 0
+    assert got.inf == (inf_v, 0.0, float("inf"))
 
 
 def test_mixture4096_bit_exact():
@@ -160,17 +163,26 @@ def test_invalid_arguments():
     assert lib.ph0_workspace_bytes(65536, 3) == 0
     assert lib.ph0_workspace_bytes(10, 2000) == 0
     ws = torch.empty(lib.ph0_workspace_bytes(10, 3), dtype=torch.uint8, device="cuda")
-    pts = torch.zeros((10, 3), device="cuda")
+    pts = torch.from_numpy(inputs.uniform(10, 3, seed=46)).cuda()
     bars = torch.empty((9, 40), dtype=torch.uint8, device="cuda")
+    inf = torch.full((24,), 0xAB, dtype=torch.uint8, device="cuda")
     vp = ctypes.c_void_p
-    args = (vp(pts.data_ptr()), 10, 3, 3, vp(bars.data_ptr()), vp(ws.data_ptr()), ws.numel(), None)
+    args = (vp(pts.data_ptr()), 10, 3, 3, vp(bars.data_ptr()), vp(inf.data_ptr()), vp(ws.data_ptr()),
+            ws.numel(), None)
     assert lib.ph0_barcodes(*args) == 0
+    st = _lib.Stats()
+    assert lib.ph0_finish(vp(ws.data_ptr()), None, ctypes.byref(st)) == 0
+    # the bar that never dies, through the C ABI: vertex 0, birth 0, death +inf
+    b = _lib.InfBar.from_buffer_copy(inf.cpu().numpy().tobytes())
+    assert (b.vertex, b.birth, b.death) == (0, 0.0, float("inf")) and st.inf_vertex == 0
+    assert lib.ph0_barcodes(*args[:5], None, *args[6:]) == 0                    # inf may be null
     assert lib.ph0_finish(vp(ws.data_ptr()), None, None) == 0
     assert lib.ph0_barcodes(args[0], 10, 3, 2, *args[4:]) == 1                  # ld < d
     assert lib.ph0_barcodes(args[0], 0, 3, 3, *args[4:]) == 1                   # n < 1
     assert lib.ph0_barcodes(args[0], 70000, 3, 3, *args[4:]) == 3               # n too big
-    assert lib.ph0_barcodes(*args[:5], args[5], ws.numel() - 1, None) == 4     # small ws
-    assert lib.ph0_barcodes(*args[:5], vp(ws.data_ptr() + 8), ws.numel(), None) == 1  # misaligned
+    assert lib.ph0_barcodes(*args[:6], args[6], ws.numel() - 1, None) == 4     # small ws
+    assert lib.ph0_barcodes(*args[:6], vp(ws.data_ptr() + 8), ws.numel(), None) == 1  # misaligned
+    assert lib.ph0_barcodes(*args[:5], vp(inf.data_ptr() + 4), *args[6:]) == 1  # misaligned inf
 
 
 def test_step_oracle_pins_hold_on_gpu_output():

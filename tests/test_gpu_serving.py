@@ -52,6 +52,7 @@ def test_fused_small_batch_equals_plain_and_oracle():
     for i, x in enumerate(clouds):
         f = done[i]
         assert f.status == 0
+        assert f.inf_vertex == 0  # the bar that never dies, written by the fused kernel
         if len(x) > 1:
             _same(f.bars, _plain(x))
         if i % 10 == 0:
@@ -69,6 +70,7 @@ def test_mixed_stream_equals_plain_under_tight_budget():
         done = run_stream(srv, clouds)
     for i, x in enumerate(clouds):
         assert done[i].status == 0
+        assert done[i].inf_vertex == 0
         _same(done[i].bars, _plain(x))
 
 
