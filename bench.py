@@ -142,6 +142,25 @@ def time_oracle(x: np.ndarray):
     return m / dt, dt, n, m
 
 
+def time_paper_cpu(x: np.ndarray, gpu_bars=None):
+    """The paper-style CPU baseline (OpenMP, all host cores) on the whole
+    cloud, once; its bars are compared with the GPU's."""
+    import oracle
+    n = len(x)
+    m = n * (n - 1) // 2
+    t0 = time.perf_counter()
+    b, _, _ = oracle.barcodes_paper_cpu(x)
+    dt = time.perf_counter() - t0
+    out = {"value": m / dt, "unit": "edges/s", "cores": oracle.paper_cpu_threads(),
+           "kind": "paper-style OpenMP CPU program (Sec. 3): parallel distance loop, parallel merge sort, "
+                   "parallel de-duplication, sequential reduction stopping at n-1 pivots",
+           "sample": f"the whole cloud: N={n}, {m} edges, {dt:.1f} s",
+           "affinity_cores": len(os.sched_getaffinity(0))}
+    if gpu_bars is not None:
+        out["bars_identical_to_gpu"] = b.tobytes() == gpu_bars.cpu().numpy().tobytes()
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, on a bounded sample."""
     if rank != 0:
@@ -324,12 +343,23 @@ def run_ours(args, rank, world, local_rank):
     # de-duplication scan, reduction (init, kernel), pivot-order sort (sort
     # init, key stats, 8 passes), emission, the infinite bar
     launches_per_step = 1 + 1 + 6 + 2 + (1 + 1 + 8 + 1) + 1 + 2 + (1 + 1 + 8) + 1 + 1
-    cpu = None
+    cpu = cpu_all = cpu_full = None
     if world == 1 and not args.no_cpu_baseline:
         r, dt, ns, ms_ = time_oracle(x)
         cpu = {"value": r, "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": f"every {SAMPLE_STRIDE}th point of the cloud: N={ns}, {ms_} edges, "
                          f"{dt:.1f} s single-threaded"}
+        # the paper-style multi-core CPU program (OpenMP loops, sequential
+        # reduction) on the whole cloud, once; it computes the same bars
+        cpu_all = time_paper_cpu(x, bars)
+        if args.cpu_full_oracle:  # the single-threaded oracle on the whole cloud (minutes, ~40 GB)
+            import oracle
+            t0 = time.perf_counter()
+            want, _, _ = oracle.barcodes(x)
+            dt = time.perf_counter() - t0
+            same = want.tobytes() == bars.cpu().numpy().tobytes()
+            cpu_full = {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle", "seconds": dt,
+                        "sample": "the whole cloud", "bars_identical_to_gpu": same}
     serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
     line = {
         "metric": METRIC, "value": job_throughput(m, world, ms), "unit": "edges/s",
@@ -349,6 +379,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline_other": roof_other,
         "phase": phase,
         "cpu_baseline": cpu,
+        "cpu_baseline_allcores": cpu_all,
+        "cpu_baseline_full_oracle": cpu_full,
         "tuning": tuning,
         "serving": serving,
         "early_exit": early,
@@ -448,6 +480,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full-oracle", action="store_true",
+                    help="also time the single-threaded oracle on the whole cloud (minutes, ~40 GB of host memory)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
     ap.add_argument("--no-early", action="store_true", help="skip timing the early-terminating path")
     ap.add_argument("--serve-clouds", type=int, default=10000,

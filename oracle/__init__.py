@@ -14,6 +14,10 @@ imports nothing from it.
 Pins that keep the oracle honest live in ``tests/test_oracle_*.py``; the
 functions here with no such pin are listed there as "parity unpinned" (none at
 present).
+
+``barcodes_paper_cpu`` is not the oracle: it wraps ``paper_cpu.c``, the
+paper-style multi-core CPU baseline (OpenMP loops, Sec. 3) that the benchmark
+times beside the GPU path; the CPU tests check it against the oracle.
 """
 from __future__ import annotations
 
@@ -40,16 +44,26 @@ BAR_DTYPE = np.dtype([
 ])
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (host architecture, no native tuning)."""
+_PAPER_SRC = os.path.join(_HERE, "paper_cpu.c")
+_PAPER_LIB = os.path.join(_OUT_DIR, "libph0_paper_cpu.so")
+_paper = None
+
+
+def _compile(src: str, out: str, flags, force: bool) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    stale = not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src)
     if force or stale:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *flags, "-o", tmp, src, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (and the paper-style CPU baseline) with gcc (host
+    architecture, no native tuning)."""
+    _compile(_PAPER_SRC, _PAPER_LIB, [*_CFLAGS, "-fopenmp"], force)
+    return _compile(_SRC, _LIB_PATH, _CFLAGS, force)
 
 
 def _load():
@@ -233,3 +247,39 @@ def pipeline(x):
     return dict(u=u, v=v, d2=d2, order=order, u_sorted=us, v_sorted=vs,
                 d2_sorted=d2s, a=a, n_distinct=nd, low=low, pivot_of=pivot_of,
                 steps=steps, bars=bars, inf_vertex=inf_v)
+
+
+def _load_paper():
+    global _paper
+    with _lock:
+        if _paper is None:
+            build()
+            lib = ctypes.CDLL(_PAPER_LIB)
+            i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+            lib.ph0p_barcodes.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
+            lib.ph0p_barcodes.restype = ctypes.c_int
+            lib.ph0p_threads.argtypes = []
+            lib.ph0p_threads.restype = ctypes.c_int
+            _paper = lib
+    return _paper
+
+
+def paper_cpu_threads() -> int:
+    """Threads the paper-style CPU baseline runs on (OpenMP's default: every
+    core the process may use, or OMP_NUM_THREADS)."""
+    return int(_load_paper().ph0p_threads())
+
+
+def barcodes_paper_cpu(x):
+    """The paper-style multi-core CPU baseline (not the oracle): the same
+    (bars, infinite-bar vertex, |D|) as barcodes(), computed with OpenMP
+    loops (Sec. 3) and a sequential reduction that stops at n-1 pivots."""
+    x = _points(x)
+    n, d = x.shape
+    bars = np.zeros(max(n - 1, 1), BAR_DTYPE)
+    nb = ctypes.c_int64(0)
+    inf_v = ctypes.c_int32(-1)
+    nd = ctypes.c_int64(0)
+    _check(_load_paper().ph0p_barcodes(_ptr(x), n, d, d, _ptr(bars), ctypes.byref(nb),
+                                       ctypes.byref(inf_v), ctypes.byref(nd)), "paper_cpu")
+    return bars[: nb.value].copy(), int(inf_v.value), int(nd.value)
