@@ -38,8 +38,10 @@
  * device-detected errors (non-finite input, a bounded wait that timed out) in
  * the workspace, where ph0_finish() reads them.
  *
- * Limits: 1 <= N <= 65535 (vertex ids are packed into 16 bits, so E < 2^31),
- * 1 <= d <= 1024.
+ * Limits: 1 <= N <= 92681 (E = N(N-1)/2 < 2^32, so every position, count
+ * and index a is a 32-bit number; the N = 92681 workspace is about 113 GB)
+ * for the whole-path entry points, 1 <= N <= 65535 for the step entry points
+ * (whose edge records pack (u << 16) | v), 1 <= d <= 1024.
  */
 #ifndef PH0_H
 #define PH0_H
@@ -55,7 +57,7 @@ typedef enum {
     PH0_OK = 0,
     PH0_EINVAL = 1,      /* bad argument: n < 1, d < 1, ld < d, null or misaligned pointer */
     PH0_ENONFINITE = 2,  /* a coordinate is NaN or +-Inf (detected on the device) */
-    PH0_ETOOBIG = 3,     /* n > 65535 or d > 1024 */
+    PH0_ETOOBIG = 3,     /* n > 92681 (65535 for the step entry points) or d > 1024 */
     PH0_ENOMEM = 4,      /* workspace smaller than ph0_workspace_bytes() */
     PH0_ETIMEOUT = 5,    /* a bounded device-side wait gave up (the kernel returned cleanly) */
     PH0_ECUDA = 6,       /* a CUDA runtime call failed */
@@ -144,7 +146,11 @@ typedef struct {
                                reduction gives up with PH0_ETIMEOUT (the kernel then
                                returns and the workspace stays usable); -1 = built-in
                                (2^24, about a second); 0 gives up at the first poll    */
-    int32_t reserved[4];
+    int32_t wide_ids;       /* 1: edge records hold the edge's lexicographic index
+                               instead of (u << 16) | v, as they always do above 65535
+                               points (test aid: runs the large-cloud form on any n);
+                               -1 or 0: only above 65535 points                          */
+    int32_t reserved[3];
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits
@@ -252,7 +258,7 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
  * device memory (every GPU that loads the library holds it until the
  * process exits); the caller still passes the points and the outputs.
  * Clouds whose workspace would exceed 16 MiB (ph0_workspace_bytes(n, d) >
- * 16 MiB: n above 934 at d = 3, above 928 at d = 32) are rejected with
+ * 16 MiB: n above 889 at d = 3, above 883 at d = 32) are rejected with
  * PH0_ETOOBIG before any work is queued.  It allocates nothing (no
  * cudaMalloc, cudaFree or allocating library call).
  *

@@ -83,6 +83,7 @@ def _load():
                 "ph0o_reduce_dense": [i64, vp, vp, vp, i64, vp, vp, vp],
                 "ph0o_barcodes": [vp, i64, i32, i64, vp, vp, vp, vp],
                 "ph0o_death_gradient": [vp, i64, i32, i64, vp, vp, vp, i64, vp],
+                "ph0o_barcodes_below": [vp, i64, i32, i64, ctypes.c_double, vp, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -203,6 +204,23 @@ def barcodes(x):
                                  ctypes.byref(inf_v), ctypes.byref(nd)),
            "barcodes")
     return bars[: nb.value].copy(), int(inf_v.value), int(nd.value)
+
+
+def barcodes_below(x, t_max: float):
+    """The bars whose squared death is at most t_max, computed from the
+    prefix of the filtration alone (edges with d2 <= t_max): (bars, edges
+    kept, distinct distances among them).  With t_max at least the largest
+    death these are exactly barcodes()'s bars, positions and indices
+    included."""
+    x = _points(x)
+    n, d = x.shape
+    bars = np.zeros(max(n - 1, 1), BAR_DTYPE)
+    nb = ctypes.c_int64(0)
+    kept = ctypes.c_int64(0)
+    nd = ctypes.c_int64(0)
+    _check(_load().ph0o_barcodes_below(_ptr(x), n, d, d, float(t_max), _ptr(bars), ctypes.byref(nb),
+                                       ctypes.byref(kept), ctypes.byref(nd)), "barcodes_below")
+    return bars[: nb.value].copy(), int(kept.value), int(nd.value)
 
 
 def death_gradient(x64, bar_u, bar_v, dl_ddeath):

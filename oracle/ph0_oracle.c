@@ -444,3 +444,86 @@ int ph0o_distances_f64(const double *x, int64_t n, int32_t d, int64_t ld,
 }
 
 int ph0o_abi_version(void) { return 1; }
+
+/* --------------------------------------------------------------------------
+ * The whole path restricted to a prefix of the filtration: only the edges
+ * whose squared distance is at most t_max enter the sort, the index a and
+ * the reduction (Sec. 2, on the edges of VR at epsilon^2 = t_max).  Every
+ * edge of the total order (d2, u, v) that comes before a kept edge is itself
+ * kept, so a kept edge's position in the prefix is its position in the whole
+ * sorted list, and its a counts the same distinct distances; the bars found
+ * are exactly those of ph0o_barcodes whose death_sq is at most t_max (all
+ * n - 1 of them when t_max is at least the largest death).  Memory and sort
+ * time scale with the kept edges, which lets the oracle check the positions
+ * and indices of every bar of clouds too large for ph0o_barcodes.
+ * Outputs: bars (room for n - 1), their count, the edges kept, and the
+ * distinct distances among them.
+ * ------------------------------------------------------------------------ */
+int ph0o_barcodes_below(const float *x, int64_t n, int32_t d, int64_t ld,
+                        double t_max, ph0o_bar *bars, int64_t *n_bars,
+                        int64_t *n_kept, int64_t *n_distinct_out)
+{
+    edge_rec *r = NULL;
+    int64_t cap = 0, k = 0, nb = 0, n_distinct = 0;
+    int32_t *us = NULL, *vs = NULL, *low = NULL;
+    int64_t *pivot_of = NULL;
+    double *d2s = NULL;
+    uint32_t *a = NULL;
+    int rc = OK;
+    if (n < 1 || d < 1 || ld < d) return ERR_ARG;
+    /* step 1, keeping the edges of the prefix */
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            const double s2 = squared_distance(x, ld, d, i, j);
+            if (!(s2 <= t_max)) continue;
+            if (k == cap) {
+                int64_t nc = cap ? cap * 2 : 1024;
+                edge_rec *p = (edge_rec *)realloc(r, (size_t)nc * sizeof(edge_rec));
+                if (!p) { rc = ERR_MEM; goto done; }
+                r = p;
+                cap = nc;
+            }
+            r[k].d2 = s2;
+            r[k].u = (int32_t)i;
+            r[k].v = (int32_t)j;
+            r[k].id = k;
+            ++k;
+        }
+    /* step 2 */
+    if (k > 0) qsort(r, (size_t)k, sizeof(edge_rec), cmp_edge);
+    us = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+    vs = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+    low = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+    d2s = (double *)malloc((size_t)(k + 1) * sizeof(double));
+    a = (uint32_t *)malloc((size_t)(k + 1) * sizeof(uint32_t));
+    pivot_of = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!us || !vs || !low || !d2s || !a || !pivot_of) { rc = ERR_MEM; goto done; }
+    for (int64_t p = 0; p < k; ++p) {
+        us[p] = r[p].u;
+        vs[p] = r[p].v;
+        d2s[p] = r[p].d2;
+    }
+    free(r);
+    r = NULL;
+    /* steps 3-5 on the prefix */
+    if ((rc = ph0o_dedupe(d2s, k, a, &n_distinct)) != OK) goto done;
+    if ((rc = ph0o_reduce(n, us, vs, k, low, pivot_of, 0)) != OK) goto done;
+    for (int64_t p = 0; p < k; ++p) {
+        if (low[p] < 0) continue;
+        if (nb >= n - 1) { rc = ERR_STATE; goto done; }
+        bars[nb].u = us[p];
+        bars[nb].v = vs[p];
+        bars[nb].a = a[p];
+        bars[nb].low = low[p];
+        bars[nb].order = p;
+        bars[nb].death_sq = d2s[p];
+        bars[nb].death = sqrt(d2s[p]);
+        ++nb;
+    }
+    *n_bars = nb;
+    *n_kept = k;
+    *n_distinct_out = n_distinct;
+done:
+    free(r); free(us); free(vs); free(low); free(d2s); free(a); free(pivot_of);
+    return rc;
+}

@@ -54,13 +54,13 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("dist_split16", ctypes.c_int32), ("dist_tile", ctypes.c_int32),
                 ("sort_top_bits", ctypes.c_int32), ("reduce_spin_limit", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("wide_ids", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     @classmethod
-    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1):
+    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1, wide_ids=-1):
         t = cls()
         t.dist_split16, t.dist_tile, t.sort_top_bits = dist_split16, dist_tile, sort_top_bits
-        t.reduce_spin_limit = reduce_spin_limit
+        t.reduce_spin_limit, t.wide_ids = reduce_spin_limit, wide_ids
         return t
 
     def as_dict(self):

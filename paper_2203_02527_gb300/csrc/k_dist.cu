@@ -72,7 +72,7 @@ template <int D, int BT>
 __global__ void __launch_bounds__(kDistThreads)
 k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16,
        uint64_t *__restrict__ key, uint32_t *__restrict__ val, Header *__restrict__ h,
-       const int32_t *gate) {
+       const int32_t *gate, int wide) {
     if (gate && ld_volatile(gate) == 0) return;  // a gated run (the sort's fallback) that is not needed
     if constexpr (D > 0) {
         d = D;
@@ -166,7 +166,7 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     auto emit = [&](int u, uint64_t kb) {
         const int64_t e = edge_index(n, u, v);
         key[e] = kb;
-        val[e] = (uint32_t(u) << 16) | uint32_t(v);
+        val[e] = wide ? uint32_t(e) : (uint32_t(u) << 16) | uint32_t(v);  // wide: the edge index
 #pragma unroll
         for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
         atomicAdd(&s_top[(kb >> kTopShift) & (kMaxRadix - 1)], 1u);
@@ -241,7 +241,7 @@ int dist_tile(int d, int want) {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
                         uint32_t *val, Header *h, cudaStream_t s, int split16, int tile,
-                        const int32_t *gate) {
+                        const int32_t *gate, bool wide) {
     if (n < 2) return cudaSuccess;
     const int bt = dist_tile(d, tile);
     const size_t smem = dist_smem(bt, d);
@@ -252,7 +252,8 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return e;
-        kernel<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, hw16, key, val, h, gate);
+        kernel<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, hw16, key, val, h, gate,
+                                                           wide ? 1 : 0);
         return cudaGetLastError();
     };
 #define PH0_DIST_CASE(DD)                                       \

@@ -43,6 +43,7 @@
 // Early exit: once n-1 pivots exist every later column is zero (the graph is
 // connected); the window loop stops.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "ph0_common.cuh"
 
@@ -52,7 +53,6 @@ constexpr int kReduceThreads = 512;
 constexpr int kFilterLoads = 4;
 constexpr int kHashSize = 2048;
 constexpr uint32_t kEmpty = 0xffffffffu;
-constexpr uint32_t kDead = 0xffffffffu;
 
 
 __global__ void k_reduce_init(ReduceArgs A) {
@@ -164,19 +164,31 @@ __device__ __forceinline__ uint16_t local_find(uint16_t *par, uint16_t x) {
 // (the snapshot array is reused as the global->local map), so every find,
 // claim and link is a shared-memory access and rounds are separated by
 // __syncthreads instead of grid barriers.  Returns the number of rounds.
+// Vertex ids in the tail's shared arrays: 16 bits, or 32 (wide records).
+template <bool WIDE>
+using TailRoot = typename std::conditional<WIDE, uint32_t, uint16_t>::type;
+
+template <bool WIDE>
 __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *val,
                                 const uint32_t *list, uint32_t ncur, uint16_t *s_comp,
                                 unsigned char *s_tail, uint32_t target, uint32_t &claims) {
     constexpr int C = kTailCap;
+    using R = TailRoot<WIDE>;
     uint32_t *s_p = reinterpret_cast<uint32_t *>(s_tail);        // [C] position
     uint32_t *s_lres = s_p + C;                                   // [2C] claim per local root
-    uint16_t *s_lu = reinterpret_cast<uint16_t *>(s_lres + 2 * C);  // [C] local root, u side
+    R *s_ra = reinterpret_cast<R *>(s_lres + 2 * C);              // [C] this round's roots
+    R *s_rb = s_ra + C;
+    R *s_gid = s_rb + C;                                          // [2C] global id
+    uint16_t *s_lu = reinterpret_cast<uint16_t *>(s_gid + 2 * C);  // [C] local root, u side
     uint16_t *s_lv = s_lu + C;                                    // [C] local root, v side
-    uint16_t *s_ra = s_lv + C;                                    // [C] this round's roots
-    uint16_t *s_rb = s_ra + C;
-    uint16_t *s_lpar = s_rb + C;                                  // [2C] local parent
-    uint16_t *s_gid = s_lpar + 2 * C;                             // [2C] global id
-    uint8_t *s_act = reinterpret_cast<uint8_t *>(s_gid + 2 * C);  // [C] still active
+    uint16_t *s_lpar = s_lv + C;                                  // [2C] local parent
+    uint8_t *s_act = reinterpret_cast<uint8_t *>(s_lpar + 2 * C);  // [C] still active
+    // the map global root -> local id: the snapshot array (its window is
+    // over), or for wide records the workspace's gmap (32-bit entries)
+    auto map_get = [&](R g) -> uint32_t {
+        if constexpr (WIDE) return __ldcg(A.gmap + g);
+        else return s_comp[g];
+    };
     __shared__ uint32_t s_nroots, s_left;
     const int tid = threadIdx.x;
     const int T = blockDim.x;
@@ -187,37 +199,50 @@ __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *
     // global roots and window-start roots of every endpoint
     for (uint32_t i = tid; i < ncur; i += T) {
         const uint32_t p = __ldcg(list + i);
-        const uint32_t vv = val[p];
-        const uint32_t u = vv >> 16, v = vv & 0xffffu;
+        uint32_t u, v;
+        record_uv(val[p], WIDE, A.n, u, v);
         s_p[i] = p;
-        s_ra[i] = uint16_t(find_root(A.parent, __ldcg(A.comp + u)));
-        s_rb[i] = uint16_t(find_root(A.parent, __ldcg(A.comp + v)));
+        s_ra[i] = R(find_root(A.parent, __ldcg(A.comp + u)));
+        s_rb[i] = R(find_root(A.parent, __ldcg(A.comp + v)));
         s_act[i] = 1;
     }
     __syncthreads();
-    // local ids: s_comp becomes the map global root -> local id
+    // local ids: the map's entries of these roots are set to "unseen", then
+    // the first thread to claim a root gives it the next local id
     for (uint32_t i = tid; i < ncur; i += T) {
-        s_comp[s_ra[i]] = 0xffffu;
-        s_comp[s_rb[i]] = 0xffffu;
+        if constexpr (WIDE) {
+            A.gmap[s_ra[i]] = 0xffffffffu;
+            A.gmap[s_rb[i]] = 0xffffffffu;
+        } else {
+            s_comp[s_ra[i]] = 0xffffu;
+            s_comp[s_rb[i]] = 0xffffu;
+        }
     }
+    __threadfence_block();
     __syncthreads();
     for (uint32_t i = tid; i < ncur; i += T) {
         for (int side = 0; side < 2; ++side) {
-            const uint16_t g = side ? s_rb[i] : s_ra[i];
-            if (atomicCAS(reinterpret_cast<unsigned short *>(s_comp + g), (unsigned short)0xffffu,
-                          (unsigned short)0xfffeu) == 0xffffu) {
+            const R g = side ? s_rb[i] : s_ra[i];
+            bool first;
+            if constexpr (WIDE) first = atomicCAS(A.gmap + g, 0xffffffffu, 0xfffffffeu) == 0xffffffffu;
+            else
+                first = atomicCAS(reinterpret_cast<unsigned short *>(s_comp + g), (unsigned short)0xffffu,
+                                  (unsigned short)0xfffeu) == 0xffffu;
+            if (first) {
                 const uint32_t id = atomicAdd(&s_nroots, 1u);
                 s_gid[id] = g;
                 s_lpar[id] = uint16_t(id);
                 s_lres[id] = 0xffffffffu;
-                s_comp[g] = uint16_t(id);
+                if constexpr (WIDE) atomicExch(A.gmap + g, id);
+                else s_comp[g] = uint16_t(id);
             }
         }
     }
+    __threadfence_block();
     __syncthreads();
     for (uint32_t i = tid; i < ncur; i += T) {
-        s_lu[i] = s_comp[s_ra[i]];
-        s_lv[i] = s_comp[s_rb[i]];
+        s_lu[i] = uint16_t(map_get(s_ra[i]));
+        s_lv[i] = uint16_t(map_get(s_rb[i]));
     }
     __syncthreads();
     uint32_t rounds = 0;
@@ -230,8 +255,8 @@ __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *
                 s_act[i] = 0;
                 continue;
             }
-            s_ra[i] = a;
-            s_rb[i] = b;
+            s_ra[i] = R(a);
+            s_rb[i] = R(b);
             atomicMin(s_lres + a, s_p[i]);
             atomicMin(s_lres + b, s_p[i]);
             claims += 2;
@@ -240,7 +265,7 @@ __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *
         uint32_t left = 0;
         for (uint32_t i = tid; i < ncur; i += T) {
             if (!s_act[i]) continue;
-            const uint16_t a = s_ra[i], b = s_rb[i];
+            const uint16_t a = uint16_t(s_ra[i]), b = uint16_t(s_rb[i]);
             const uint32_t p = s_p[i];
             const bool a_lo = s_gid[a] < s_gid[b];
             const uint16_t lo = a_lo ? a : b, hi = a_lo ? b : a;
@@ -275,11 +300,23 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
+// WIDE (records hold edge indices, n up to kMaxNWide): the window's root
+// snapshot is read from the global root table instead of a 16-bit copy in
+// shared memory, and root pairs are 64-bit hash keys.
+template <bool WIDE>
 __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
-    extern __shared__ uint16_t s_comp[];  // [n] root snapshot of the window
-    __shared__ uint32_t s_hkey[kHashSize], s_hval[kHashSize];
+    using PairT = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    constexpr PairT kPairEmpty = ~PairT(0);
+    extern __shared__ uint16_t s_comp[];  // [n] root snapshot of the window (not WIDE)
+    __shared__ PairT s_hkey[kHashSize];
+    __shared__ uint32_t s_hval[kHashSize];
     __shared__ uint32_t s_hcount;
     __shared__ int s_ok;
+    // snapshot root of vertex x at the window start
+    auto snap = [&](uint32_t x) -> uint32_t {
+        if constexpr (WIDE) return __ldcg(A.comp + x);
+        else return s_comp[x];
+    };
 
     Header *h = A.h;
     const int64_t n = A.n, m = A.m;
@@ -315,9 +352,10 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         }
 
         // ---------------- F: filter the window against the snapshot -------
-        for (int64_t v = tid; v < n; v += kReduceThreads) s_comp[v] = uint16_t(__ldcg(A.comp + v));
+        if constexpr (!WIDE)
+            for (int64_t v = tid; v < n; v += kReduceThreads) s_comp[v] = uint16_t(__ldcg(A.comp + v));
         for (int i = tid; i < kHashSize; i += kReduceThreads) {
-            s_hkey[i] = kEmpty;
+            s_hkey[i] = kPairEmpty;
             s_hval[i] = kEmpty;
         }
         if (tid == 0) s_hcount = 0;
@@ -352,11 +390,15 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
                 if (p < wend) {
                     uint32_t vv = vq[qr];
-                    if ((vv >> 16) >= n || (vv & 0xffffu) >= n) {  // corrupt input: never index past n
+                    // corrupt input: never index past n
+                    const bool bad = WIDE ? int64_t(vv) >= A.m_edges : ((vv >> 16) >= n || (vv & 0xffffu) >= n);
+                    if (bad) {  // reported, and never a candidate
                         set_status(h, PH0_EINTERNAL);
-                        vq[qr] = vv = 0;
+                    } else {
+                        uint32_t u, v;
+                        record_uv(vv, WIDE, n, u, v);
+                        if (snap(u) != snap(v)) differ |= 1u << qr;
                     }
-                    if (s_comp[vv >> 16] != s_comp[vv & 0xffffu]) differ |= 1u << qr;
                 }
             }
             if (!__any_sync(0xffffffffu, differ != 0)) continue;
@@ -365,25 +407,26 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             for (int qr = 0; qr < kFilterLoads * 4; ++qr) {
                 const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
                 if ((differ >> qr) & 1u) {
-                    const uint32_t vv = vq[qr];
-                    const uint32_t cu = s_comp[vv >> 16], cv = s_comp[vv & 0xffffu];
+                    uint32_t u, v;
+                    record_uv(vq[qr], WIDE, n, u, v);
+                    const uint32_t cu = snap(u), cv = snap(v);
                     const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
-                    const uint32_t pair = (lo << 16) | hi;
+                    const PairT pair = (PairT(lo) << (WIDE ? 32 : 16)) | hi;
                     bool done = false;
                     if (*(volatile uint32_t *)&s_hcount < kHashSize / 2) {
-                        const uint32_t hs = (pair * 2654435761u) >> 21;  // 11 bits
+                        const uint32_t hs = (uint32_t(pair ^ (pair >> 29)) * 2654435761u) >> 21;  // 11 bits
                         for (int pr = 0; pr < 8; ++pr) {
                             const uint32_t slot = (hs + pr) & (kHashSize - 1);
                             // a slot keeps its pair for the whole window, so a plain
                             // read that finds it needs no CAS; the minimum only
                             // falls, so a plain read at or below p needs no atomic
                             // (every record of a pair hits one slot: no contention)
-                            uint32_t old = *(volatile uint32_t *)&s_hkey[slot];
+                            PairT old = *(volatile PairT *)&s_hkey[slot];
                             if (old != pair) {
-                                old = atomicCAS(&s_hkey[slot], kEmpty, pair);
-                                if (old == kEmpty) atomicAdd(&s_hcount, 1u);
+                                old = atomicCAS(&s_hkey[slot], kPairEmpty, pair);
+                                if (old == kPairEmpty) atomicAdd(&s_hcount, 1u);
                             }
-                            if (old == kEmpty || old == pair) {
+                            if (old == kPairEmpty || old == pair) {
                                 if (*(volatile uint32_t *)&s_hval[slot] > uint32_t(p))
                                     atomicMin(&s_hval[slot], uint32_t(p));
                                 done = true;
@@ -403,7 +446,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         }
         __syncthreads();
         for (int slot = tid; slot < kHashSize; slot += kReduceThreads) {
-            const bool has = s_hkey[slot] != kEmpty;
+            const bool has = s_hkey[slot] != kPairEmpty;
             warp_append(has, s_hval[slot], A.cand0, &h->nlist[0]);
         }
         if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
@@ -427,13 +470,14 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             // claim both current roots
             for (int64_t i = gtid; i < ncur; i += gstride) {
                 const uint32_t p = __ldcg(list + i);
-                const uint32_t vv = val[p];
-                const uint32_t ru = find_root(A.parent, __ldcg(A.comp + (vv >> 16)));
-                const uint32_t rv = find_root(A.parent, __ldcg(A.comp + (vv & 0xffffu)));
+                uint32_t u, v;
+                record_uv(val[p], WIDE, n, u, v);
+                const uint32_t ru = find_root(A.parent, __ldcg(A.comp + u));
+                const uint32_t rv = find_root(A.parent, __ldcg(A.comp + v));
                 if (ru == rv) {
-                    A.candr[i] = kDead;
+                    A.candr[i] = ~0ull;
                 } else {
-                    A.candr[i] = (ru << 16) | rv;
+                    A.candr[i] = (static_cast<unsigned long long>(ru) << 32) | rv;
                     atomicMin(A.res + ru, tag | p);
                     atomicMin(A.res + rv, tag | p);
                     claims += 2;
@@ -446,10 +490,10 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 bool keep = false;
                 uint32_t p = 0;
                 if (i < ncur) {
-                    const uint32_t r = __ldcg(A.candr + i);
-                    if (r != kDead) {
+                    const unsigned long long r = __ldcg(A.candr + i);
+                    if (r != ~0ull) {
                         p = __ldcg(list + i);
-                        const uint32_t ru = r >> 16, rv = r & 0xffffu;
+                        const uint32_t ru = uint32_t(r >> 32), rv = uint32_t(r);
                         const uint32_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
                         if (__ldcg(A.res + hi) == (tag | p)) {
                             A.parent[hi] = lo;
@@ -469,9 +513,10 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         if (ncur > 0) {
             // few candidates left: one CTA finishes the window in shared memory
             if (blockIdx.x == 0)
-                tail_total += tail_rounds(A, h, val, cur ? A.cand1 : A.cand0, ncur, s_comp,
-                                          reinterpret_cast<unsigned char *>(s_comp + ((n + 7) & ~int64_t(7))),
-                                          target, claims);
+                tail_total += tail_rounds<WIDE>(
+                    A, h, val, cur ? A.cand1 : A.cand0, ncur, s_comp,
+                    reinterpret_cast<unsigned char *>(s_comp + (WIDE ? 0 : ((n + 7) & ~int64_t(7)))), target,
+                    claims);
             if (!grid_barrier(h, &s_ok, A.spin_limit)) return;
         }
 
@@ -518,7 +563,7 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
                        const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                        const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                        const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                       const uint32_t *cpref, ph0_bar *bars) {
+                       const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n) {
     const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
     const int lane = threadIdx.x & 31;
     if (j >= nb) return;
@@ -550,11 +595,12 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
     }
     if (lane != 0) return;
     atomicXor(&h->inf_xor, low);
-    const uint32_t vv = sodd ? val1[p] : val0[p];
+    uint32_t u, v;
+    record_uv(sodd ? val1[p] : val0[p], wide, n, u, v);
     const uint64_t key = keys[p];
     ph0_bar b;
-    b.u = int32_t(vv >> 16);
-    b.v = int32_t(vv & 0xffffu);
+    b.u = int32_t(u);
+    b.v = int32_t(v);
     b.a = aval;
     b.low = int32_t(low);
     b.order = int64_t(p);
@@ -592,10 +638,12 @@ cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Snapshot labels (2 B per vertex, rounded up to 16 B) plus the tail arrays.
-size_t reduce_dyn_smem(int64_t n) {
-    const size_t snap = sizeof(uint16_t) * size_t((n + 7) & ~int64_t(7));
-    const size_t tail = size_t(kTailCap) * (4 + 4 * 2 + 2 * 4 + 2 * 2 * 2 + 1);
+// Snapshot labels (2 B per vertex, rounded up to 16 B; none for wide
+// records) plus the tail arrays (global ids of 2 or 4 bytes).
+size_t reduce_dyn_smem(int64_t n, bool wide) {
+    const size_t snap = wide ? 0 : sizeof(uint16_t) * size_t((n + 7) & ~int64_t(7));
+    const size_t rid = wide ? 4 : 2;
+    const size_t tail = size_t(kTailCap) * (4 + 4 * 2 + rid * 4 + 2 * 4 + 1);
     return snap + tail;
 }
 
@@ -607,11 +655,12 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || A.m <= 0) return e;
 
-    const size_t smem = reduce_dyn_smem(A.n);
-    e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const size_t smem = reduce_dyn_smem(A.n, A.wide);
+    const void *fn = A.wide ? (const void *)k_reduce<true> : (const void *)k_reduce<false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reduce, kReduceThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kReduceThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (per_sm > 2) per_sm = 2;
@@ -621,18 +670,17 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     if (want < grid) grid = want < 4 ? 4 : int(want);
     ReduceArgs args = A;
     void *params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void *)k_reduce, dim3(grid), dim3(kReduceThreads), params,
-                                       smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kReduceThreads), params, smem, s);
 }
 
 cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        const uint32_t *cpref, ph0_bar *bars, cudaStream_t s) {
+                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
     k_emit<<<unsigned((nb + 7) / 8), 256, 0, s>>>(nb, m, h, kk0, kk1, kv0, kv1, kill_h, val0, val1, key0,
-                                                 key1, sort_h, a, cpref, bars);
+                                                 key1, sort_h, a, cpref, bars, wide, n);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ namespace ph0 {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
                         uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1,
-                        const int32_t *gate = nullptr);
+                        const int32_t *gate = nullptr, bool wide = false);
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
                              int top_bits = kDefaultTopBits, int64_t sorted_edges = -1,
                              const int32_t *gate = nullptr);
@@ -58,13 +58,15 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        const uint32_t *cpref, ph0_bar *bars, cudaStream_t s);
+                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s);
 
 namespace {
 
-int check_sizes(int64_t n, int32_t d, int64_t ld) {
+// max_n: kMaxN for the step entry points (records (u << 16) | v), kMaxNWide
+// for the whole path (edge-index records above kMaxN).
+int check_sizes(int64_t n, int32_t d, int64_t ld, int64_t max_n = kMaxN) {
     if (n < 1 || d < 1 || ld < d) return PH0_EINVAL;
-    if (n > kMaxN || d > kMaxD) return PH0_ETOOBIG;
+    if (n > max_n || d > kMaxD) return PH0_ETOOBIG;
     return PH0_OK;
 }
 
@@ -83,8 +85,11 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? PH0_OK : PH0_ECUDA; }
 struct Tune {
     int split16 = kDefaultDistSplit16, tile = -1, top_bits = kDefaultTopBits;
     uint32_t spin_limit = kSpinLimit;
-    explicit Tune(const ph0_tuning *t) {
+    bool wide = false;  // edge-index records (always above kMaxN points)
+    explicit Tune(const ph0_tuning *t, int64_t n = 0) {
+        wide = n > kMaxN;
         if (!t) return;
+        if (t->wide_ids == 1) wide = true;
         if (t->dist_split16 >= 0 && t->dist_split16 <= 16) split16 = t->dist_split16;
         if (t->dist_tile == 32 || t->dist_tile == 64 || t->dist_tile == 128) tile = t->dist_tile;
         if (t->sort_top_bits == 8 || t->sort_top_bits == 9) top_bits = t->sort_top_bits;
@@ -116,7 +121,7 @@ cudaError_t sort_fallback(void *ws, const Layout &L, const float *pts, int64_t n
     const int32_t *gate = &h->fixup_fallback;
     cudaError_t e = cudaMemsetAsync(fh, 0, kHeaderBytes, s);
     if (e == cudaSuccess) e = launch_sort_init(fh, look0, L.tiles, s, t.top_bits, -1, gate);
-    if (e == cudaSuccess) e = launch_dist(pts, n, d, ld, k0, v0, fh, s, t.split16, t.tile, gate);
+    if (e == cudaSuccess) e = launch_dist(pts, n, d, ld, k0, v0, fh, s, t.split16, t.tile, gate, t.wide);
     // persistent grids: the passes return at once unless the flag is set
     if (e == cudaSuccess) e = launch_sort_passes(k0, k1, v0, v1, L.m, look0, look1, fh, s, true);
     // the fix-up's de-duplication counts no longer hold: count again
@@ -146,7 +151,7 @@ cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, i
 // selects the one holding the sorted data) or the caller's.
 cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                        const uint32_t *val1, const Header *sort_h, cudaStream_t s,
-                       uint32_t spin_limit = kSpinLimit) {
+                       uint32_t spin_limit = kSpinLimit, bool wide = false) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -158,7 +163,10 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
     A.res = at<unsigned long long>(ws, L.res);
     A.cand0 = at<uint32_t>(ws, L.cand[0]);
     A.cand1 = at<uint32_t>(ws, L.cand[1]);
-    A.candr = at<uint32_t>(ws, L.candr);
+    A.candr = at<unsigned long long>(ws, L.candr);
+    A.gmap = at<uint32_t>(ws, L.gmap);
+    A.m_edges = n_edges(n);
+    A.wide = wide;
     A.kill_key = at<unsigned long long>(ws, L.kill_key[0]);
     A.kill_val = at<uint32_t>(ws, L.kill_val[0]);
     A.h = at<Header>(ws, L.hdr);
@@ -177,7 +185,7 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
 cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
-                           ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s) {
+                           ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s, bool wide = false) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t nb = n - 1;
     if (nb <= 0) return launch_inf(h, n, inf, s);
@@ -196,7 +204,7 @@ cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, cons
     if (e != cudaSuccess) return e;
     e = launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
                     reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
-                    key0, key1, sort_h, a, cpref, bars, s);
+                    key0, key1, sort_h, a, cpref, bars, wide, n, s);
     if (e != cudaSuccess) return e;
     return launch_inf(h, n, inf, s);
 }
@@ -206,15 +214,16 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
                             const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                             const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
                             ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s,
-                            cudaEvent_t after_reduce = nullptr, uint32_t spin_limit = kSpinLimit) {
+                            cudaEvent_t after_reduce = nullptr, uint32_t spin_limit = kSpinLimit,
+                            bool wide = false) {
     const int64_t m = n_edges(n);
-    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit);
+    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit, wide);
     if (e != cudaSuccess) return e;
     if (after_reduce) {
         e = cudaEventRecord(after_reduce, s);
         if (e != cudaSuccess) return e;
     }
-    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s);
+    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s, wide);
 }
 
 }  // namespace
@@ -229,7 +238,7 @@ const char *ph0_strerror(int status) {
         case PH0_OK: return "ok";
         case PH0_EINVAL: return "invalid argument";
         case PH0_ENONFINITE: return "non-finite coordinate";
-        case PH0_ETOOBIG: return "size above the supported maximum (n <= 65535, d <= 1024)";
+        case PH0_ETOOBIG: return "size above the supported maximum (n <= 92681, 65535 for the step calls; d <= 1024)";
         case PH0_ENOMEM: return "workspace too small";
         case PH0_ETIMEOUT: return "a bounded device-side wait timed out";
         case PH0_ECUDA: return "CUDA runtime error";
@@ -242,33 +251,33 @@ const char *ph0_strerror(int status) {
 int32_t ph0_abi_version(void) { return 3; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
-    if (check_sizes(n, d, d) != PH0_OK) return 0;
+    if (check_sizes(n, d, d, kMaxNWide) != PH0_OK) return 0;
     return Layout(n, d).total;
 }
 
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                        ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream,
                        const ph0_tuning *tuning) {
-    int rc = check_sizes(n, d, ld);
+    int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
     if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
         return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
-    const Tune t(tuning);
+    const Tune t(tuning, n);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, nullptr,
-                            t.spin_limit);
+                            t.spin_limit, t.wide);
     return cuda_status(e);
 }
 
@@ -279,7 +288,7 @@ int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar
 
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                        ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
-    int rc = check_sizes(n, d, ld);
+    int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
     if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
@@ -291,7 +300,7 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
         const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
         return r != PH0_OK ? r : ph0_finish(ws, stream, nullptr);
     };
-    if (n < 3) return whole();
+    if (n < 3 || n > kMaxN) return whole();  // wide records: the whole path
     const Tune t(nullptr);
     const int64_t m = L.m;
     Header *h = at<Header>(ws, L.hdr);
@@ -427,7 +436,7 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                           ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
                           void *stream, const ph0_tuning *tuning, ph0_profile *prof) {
-    int rc = check_sizes(n, d, ld);
+    int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || !prof || (n > 1 && !bars_dev)) return PH0_EINVAL;
     if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
@@ -453,10 +462,10 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     // dedupe | ev[3+P] | reduce | ev[4+P] | order pivots, emit | ev[5+P]
     // (P = kMaxPasses; the short sort launches the passes from slot 2 on;
     // passes that are not needed return at once)
-    const Tune t(tuning);
+    const Tune t(tuning, n);
     e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
@@ -471,7 +480,7 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 + kMaxPasses], s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, ev[4 + kMaxPasses],
-                            t.spin_limit);
+                            t.spin_limit, t.wide);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5 + kMaxPasses], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[5 + kMaxPasses]);
     if (e == cudaSuccess) {
@@ -524,7 +533,7 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
 
 int ph0_trace_windows(const void *ws, int64_t n, int32_t d, void *stream, uint64_t *out,
                       int32_t max_windows) {
-    int rc = check_sizes(n, d, d);
+    int rc = check_sizes(n, d, d, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!ws || !out || max_windows < 0) return PH0_EINVAL;
     const Layout L(n, d);
@@ -613,7 +622,7 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev, const uint32_t *a_dev,
 int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                           const ph0_bar *bars_dev, int64_t n_bars, const double *dl_ddeath_dev,
                           float *grad_dev, void *ws, size_t ws_bytes, void *stream) {
-    int rc = check_sizes(n, d, ld);
+    int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (n_bars < 0 || n_bars > n - 1) return PH0_EINVAL;
     if (!pts_dev || !grad_dev || !ws || (n_bars > 0 && (!bars_dev || !dl_ddeath_dev)))

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstddef>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -14,6 +15,11 @@ namespace ph0 {
 
 // ---------------------------------------------------------------- limits ---
 constexpr int64_t kMaxN = 65535;   // vertex ids packed in 16 bits: E < 2^31
+// Larger clouds ("wide" records): the value of an edge is its lexicographic
+// index e = u(2n-u-1)/2 + v-u-1 instead of (u << 16) | v, and every position,
+// count and index a stays below 2^32 while E = n(n-1)/2 < 2^32.
+constexpr int64_t kMaxNWide = 92681;
+static_assert(kMaxNWide * (kMaxNWide - 1) / 2 < (int64_t(1) << 32), "wide edge indices fit 32 bits");
 constexpr int32_t kMaxD = 1024;
 constexpr int kMaxPasses = 8;      // 6 low digit passes + at most 2 top passes
 constexpr int kRadixBits = 8;
@@ -136,6 +142,7 @@ struct Layout {
     size_t phist;                        // key histogram of the early-terminating path
     size_t dlook;                        // look-back words of the de-duplication scan
     size_t comp, parent, res, cand[2], candr;
+    size_t gmap;                         // [n] global root -> local id of the wide reduction's tail
     size_t kill_key[2], kill_val[2], kill_look[2];
     size_t grad;                         // binary64 gradient accumulator [n, d]
     size_t trace;                        // per-window trace records of the reduction
@@ -168,7 +175,8 @@ struct Layout {
         res = take(8 * size_t(n));
         cand[0] = take(4 * size_t(wcap + 1));
         cand[1] = take(4 * size_t(wcap + 1));
-        candr = take(4 * size_t(wcap + 1));
+        candr = take(8 * size_t(wcap + 1));
+        gmap = take(4 * size_t(n));
         kill_key[0] = take(8 * size_t(n));
         kill_key[1] = take(8 * size_t(n));
         kill_val[0] = take(4 * size_t(n));
@@ -190,7 +198,10 @@ struct ReduceArgs {
     uint32_t *parent;              // [n] link of each root claimed in this window
     unsigned long long *res;       // [n] claim of each root: (~round << 32) | position
     uint32_t *cand0, *cand1;       // candidate lists (ping-pong)
-    uint32_t *candr;               // [list] roots of each candidate in this round
+    unsigned long long *candr;     // [list] roots of each candidate in this round (ru << 32 | rv)
+    uint32_t *gmap;                // [n] global root -> local id (wide tail rounds)
+    int64_t m_edges;               // n(n-1)/2: bound of the wide records' edge indices
+    bool wide;                     // records hold edge indices (n > kMaxN, or forced)
     unsigned long long *kill_key;  // [n] position of each pivot column
     uint32_t *kill_val;            // [n] its pivot row
     Header *h;
@@ -234,6 +245,33 @@ __device__ __forceinline__ void st_volatile(uint64_t *p, uint64_t v) {
 // Edge index of (u, v), u < v, in lexicographic order.
 __host__ __device__ __forceinline__ int64_t edge_index(int64_t n, int64_t u, int64_t v) {
     return u * (2 * n - u - 1) / 2 + (v - u - 1);
+}
+
+// (u, v) of a record value: (u << 16) | v, or (wide) the edge index e < n(n-1)/2.
+// The row u of e is the largest r with r(2n-r-1)/2 <= e: the smaller root of
+// r^2 - (2n-1) r + 2e = 0, estimated in binary32 (off by at most one at
+// n < 2^17) and corrected with exact integer arithmetic.
+__host__ __device__ __forceinline__ void record_uv(uint32_t vv, bool wide, int64_t n, uint32_t &u, uint32_t &v) {
+    if (!wide) {
+        u = vv >> 16;
+        v = vv & 0xffffu;
+        return;
+    }
+    const int64_t e = int64_t(vv), b = 2 * n - 1;
+    const int64_t disc = b * b - 8 * e;  // > 0 for e < n(n-1)/2
+#ifdef __CUDA_ARCH__
+    const float root = __fsqrt_rn(float(disc));
+#else
+    const float root = sqrtf(float(disc));  // also correctly rounded
+#endif
+    int64_t r = int64_t((float(b) - root) * 0.5f);
+    r = r < 0 ? 0 : (r > n - 2 ? n - 2 : r);
+    if (r * (2 * n - r - 1) / 2 > e) --r;
+    if (r > 0 && r * (2 * n - r - 1) / 2 > e) --r;
+    if (r + 1 <= n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= e) ++r;
+    if (r + 1 <= n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= e) ++r;
+    u = uint32_t(r);
+    v = uint32_t(e - r * (2 * n - r - 1) / 2 + r + 1);
 }
 
 // Radix plan.  Bits above the highest bit in which the keys differ are

@@ -368,7 +368,7 @@ int ph0_ctx_create(const ph0_options *opt, ph0_ctx **out) {
 int ph0_submit(ph0_ctx *c, const float *pts_host, int64_t n, int32_t d, uint64_t tag) {
     if (!c || (!pts_host && n > 0)) return PH0_EINVAL;
     if (n < 1 || d < 1) return PH0_EINVAL;
-    if (n > kMaxN || d > kMaxD) return PH0_ETOOBIG;
+    if (n > kMaxNWide || d > kMaxD) return PH0_ETOOBIG;
     Request *r = new Request();
     r->tag = tag;
     r->n = int32_t(n);

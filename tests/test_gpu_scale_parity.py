@@ -55,3 +55,15 @@ def test_early_path_equals_oracle_beyond_one_window(cloud):
     assert got.stats["sorted_edges"] == len(x) * (len(x) - 1) // 2
     assert got.stats["n_distinct"] == nd
     torch.cuda.empty_cache()
+
+
+def test_large_cloud_form_equals_oracle_beyond_one_window(cloud):
+    """The same cloud through the large-cloud form (edge-index records, the
+    reduction's snapshot in global memory), forced on."""
+    from paper_2203_02527_gb300 import ph0
+    x, want, inf_v, nd = cloud
+    got = ph0.barcodes(torch.from_numpy(x).cuda(), tuning={"wide_ids": 1})
+    assert_bars_equal(got.numpy(), want)
+    assert got.stats["n_distinct"] == nd
+    assert got.inf == (inf_v, 0.0, float("inf"))
+    torch.cuda.empty_cache()

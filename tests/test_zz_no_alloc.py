@@ -81,14 +81,14 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls():
 
 def test_noalloc_size_limit_edge():
     lib = _lib().load()
-    # n = 934 at d = 3 is the largest cloud whose workspace fits 16 MiB
-    assert lib.ph0_workspace_bytes(934, 3) <= 16 << 20 < lib.ph0_workspace_bytes(935, 3)
-    x = inputs.uniform(934, 3, seed=73)
+    # n = 889 at d = 3 is the largest cloud whose workspace fits 16 MiB
+    assert lib.ph0_workspace_bytes(889, 3) <= 16 << 20 < lib.ph0_workspace_bytes(890, 3)
+    x = inputs.uniform(889, 3, seed=73)
     pts = torch.from_numpy(x).cuda()
     np.testing.assert_array_equal(_bars_noalloc(lib, pts), _oracle_raw(x))
-    y = torch.from_numpy(inputs.uniform(935, 3, seed=74)).cuda()
-    bars = torch.empty((934, 40), dtype=torch.uint8, device="cuda")
-    assert lib.ph0_barcodes_noalloc(vp(y.data_ptr()), 935, 3, 3, vp(bars.data_ptr()), None, None) == 3
+    y = torch.from_numpy(inputs.uniform(890, 3, seed=74)).cuda()
+    bars = torch.empty((889, 40), dtype=torch.uint8, device="cuda")
+    assert lib.ph0_barcodes_noalloc(vp(y.data_ptr()), 890, 3, 3, vp(bars.data_ptr()), None, None) == 3
 
 
 def test_noalloc_strided_and_trivial_clouds():
