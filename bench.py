@@ -275,7 +275,10 @@ def run_ours(args, rank, world, local_rank):
         early_t = max_over_ranks(float(np.mean(early_ms)), dev)
         early = {"value": job_throughput(m, world, early_t), "unit": "edges/s", "ms_per_step": early_t,
                  "sorted_edges": int(eb.stats["sorted_edges"]), "identical_to_whole_path": early_same,
-                 "timing": "host clock around the synchronous call, L2 flushed before each"}
+                 "timing": "host clock around the synchronous call, L2 flushed before each",
+                 "choice": "built-in (sorts in rounds from 2^27 edges on)"}
+        if rank == 0 and world == 1:
+            early["configs"] = time_early_configs(args, dev, flush)
 
     if rank != 0:
         return
@@ -389,6 +392,41 @@ def run_ours(args, rank, world, local_rank):
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def time_early_configs(args, dev, flush):
+    """ph0_barcodes_early with its built-in choice against the plain whole
+    path on the three single-cloud workloads, both on the host clock around
+    the synchronous calls (L2 flushed before each); bars compared."""
+    import torch
+
+    from paper_2203_02527_gb300 import ph0
+    out = {}
+    for name in ("uniform256", "mixture4096", "circles32768"):
+        x = inputs.config_points(name)
+        pts = torch.from_numpy(x).to(dev)
+        ws = ph0.Workspace(len(x), x.shape[1], dev)
+        times = {"whole": [], "early": []}
+        same = True
+        for i in range(args.warmup + args.steps):
+            for kind in ("whole", "early"):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b = ph0.barcodes(pts, ws) if kind == "whole" else ph0.barcodes_early(pts, ws)
+                t1 = time.perf_counter()
+                if i >= args.warmup:
+                    times[kind].append((t1 - t0) * 1e3)
+                if kind == "whole":
+                    ref = b.raw.clone()
+                else:
+                    same = same and bool(torch.equal(b.raw, ref))
+                    sorted_edges = int(b.stats["sorted_edges"])
+        out[name] = {"whole_ms": float(np.mean(times["whole"])), "early_ms": float(np.mean(times["early"])),
+                     "sorted_edges": sorted_edges, "edges": len(x) * (len(x) - 1) // 2, "identical": same}
+        del ws
+        torch.cuda.empty_cache()
+    return out
 
 
 def percentile(vals, q):

@@ -150,7 +150,10 @@ typedef struct {
                                instead of (u << 16) | v, as they always do above 65535
                                points (test aid: runs the large-cloud form on any n);
                                -1 or 0: only above 65535 points                          */
-    int32_t reserved[3];
+    int32_t early_rounds;   /* ph0_barcodes_early_tuned: 1 always sorts the prefix in
+                               rounds, 0 never (the whole path); -1 built-in: rounds
+                               only for clouds of at least 2^27 edges (n >= 16385)     */
+    int32_t reserved[2];
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits
@@ -171,6 +174,16 @@ typedef struct {
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                        ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
                        void *stream);
+
+/* ph0_barcodes_early() with a choice of path (tuning->early_rounds).  Built
+ * in (NULL or -1): below 2^27 edges the whole path runs instead of the
+ * rounds, because there the rounds' fixed cost (a host wait per round, the
+ * histogram and the class pass) exceeds what skipping the sort of the
+ * suffix saves (a 4096-point cloud: 3.2 ms in rounds against 1.2 ms whole);
+ * above 65535 points the whole path always runs.  Same results either way. */
+int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
+                             ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
+                             void *stream, const ph0_tuning *tuning);
 
 /* ph0_barcodes() with explicit tuning (NULL = built-in). */
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,

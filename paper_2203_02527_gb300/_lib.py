@@ -54,13 +54,15 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("dist_split16", ctypes.c_int32), ("dist_tile", ctypes.c_int32),
                 ("sort_top_bits", ctypes.c_int32), ("reduce_spin_limit", ctypes.c_int32),
-                ("wide_ids", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("wide_ids", ctypes.c_int32), ("early_rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     @classmethod
-    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1, wide_ids=-1):
+    def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1, wide_ids=-1,
+             early_rounds=-1):
         t = cls()
         t.dist_split16, t.dist_tile, t.sort_top_bits = dist_split16, dist_tile, sort_top_bits
-        t.reduce_spin_limit, t.wide_ids = reduce_spin_limit, wide_ids
+        t.reduce_spin_limit, t.wide_ids, t.early_rounds = reduce_spin_limit, wide_ids, early_rounds
         return t
 
     def as_dict(self):
@@ -118,6 +120,8 @@ SIGNATURES = {
     "ph0_workspace_bytes": (_SZ, [_I64, _I32]),
     "ph0_barcodes": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_barcodes_early": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP]),
+    "ph0_barcodes_early_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
+                                                ctypes.POINTER(Tuning)]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
     "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
                                           ctypes.POINTER(Tuning)]),

@@ -216,7 +216,7 @@ k_chunk_scan(uint32_t *__restrict__ cnt, int64_t chunks, uint64_t *look, Header 
         }
         if (lane < NW) s_warp[lane] = wi - w;
         const uint32_t total = __shfl_sync(0xffffffffu, wi, 31);
-        // look-back on the tile totals (chunk counts sum to at most m < 2^31)
+        // look-back on the tile totals (chunk counts sum to at most m < 2^32)
         uint32_t excl = 0;
         if (tile == 0) {
             if (lane == 0) st_volatile(look + tile, kFlagPrefix | total);

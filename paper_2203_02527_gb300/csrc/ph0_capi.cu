@@ -30,6 +30,8 @@ cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, co
                                 uint32_t *cnt, const int32_t *gate, cudaStream_t s);
 cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s);
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
+// ph0_barcodes_early's built-in choice: rounds from this many edges on
+constexpr int64_t kEarlyMinEdges = int64_t(1) << 27;
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
                                cudaStream_t s);
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s,
@@ -288,6 +290,12 @@ int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar
 
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                        ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
+    return ph0_barcodes_early_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
+}
+
+int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                             ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream,
+                             const ph0_tuning *tuning) {
     int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
@@ -300,7 +308,10 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
         const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
         return r != PH0_OK ? r : ph0_finish(ws, stream, nullptr);
     };
-    if (n < 3 || n > kMaxN) return whole();  // wide records: the whole path
+    // the whole path: tiny clouds, wide records, and (built-in choice) clouds
+    // below kEarlyMinEdges, where the rounds' fixed cost exceeds the saving
+    const int rounds = tuning ? tuning->early_rounds : -1;
+    if (n < 3 || n > kMaxN || rounds == 0 || (rounds != 1 && L.m < kEarlyMinEdges)) return whole();
     const Tune t(nullptr);
     const int64_t m = L.m;
     Header *h = at<Header>(ws, L.hdr);

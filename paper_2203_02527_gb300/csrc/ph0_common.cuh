@@ -45,7 +45,7 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kFlagMask = 3ull << 62;
 constexpr uint64_t kCountMask = ~kFlagMask;
-// Counts and prefixes stay below 2^31, so a status word's high half holds its
+// Counts and prefixes stay below 2^32, so a status word's high half holds its
 // flag alone and its low half its count; an unpublished word is all zero.
 constexpr uint32_t kHiAgg = uint32_t(kFlagAgg >> 32), kHiPrefix = uint32_t(kFlagPrefix >> 32);
 

@@ -133,16 +133,19 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     return Bars(bars, n, st, inf)
 
 
-def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None) -> Bars:
+def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None, rounds: bool | None = None) -> Bars:
     """The same bars as barcodes(), sorting only the prefix of the edge order
-    the reduction needs (ph0_barcodes_early; waits for the GPU).  The stats
-    report the prefix length as sorted_edges."""
+    the reduction needs (ph0_barcodes_early_tuned; waits for the GPU).  The
+    stats report the prefix length as sorted_edges.  rounds: None lets the
+    library choose (rounds from 2^27 edges on), True always sorts in rounds,
+    False runs the whole path."""
     pts, n, d, ld = _points(pts)
     ws = ws or _workspace(n, d, pts.device)
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     inf = _inf_buffer(pts.device)
-    check(_lib.load().ph0_barcodes_early(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
-                                         _stream()), "ph0_barcodes_early")
+    t = _lib.Tuning.make(early_rounds=-1 if rounds is None else int(bool(rounds)))
+    check(_lib.load().ph0_barcodes_early_tuned(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
+                                               _stream(), ctypes.byref(t)), "ph0_barcodes_early")
     return Bars(bars, n, finish(ws), inf)
 
 

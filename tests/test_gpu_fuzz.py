@@ -64,4 +64,4 @@ def test_random_clouds_bit_exact(seed):
         want = oracle.barcodes(x)[0]
         pts = torch.from_numpy(x).cuda()
         assert _equal(ph0.barcodes(pts).numpy(), want), (seed, kind, x.shape)
-        assert _equal(ph0.barcodes_early(pts).numpy(), want), (seed, kind, x.shape, "early")
+        assert _equal(ph0.barcodes_early(pts, rounds=True).numpy(), want), (seed, kind, x.shape, "early")
