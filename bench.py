@@ -364,6 +364,7 @@ def run_ours(args, rank, world, local_rank):
             cpu_full = {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle", "seconds": dt,
                         "sample": "the whole cloud", "bars_identical_to_gpu": same}
     serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
+    descent = run_descent(args, dev) if (world == 1 and not args.no_descent) else None
     line = {
         "metric": METRIC, "value": job_throughput(m, world, ms), "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -386,12 +387,53 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline_full_oracle": cpu_full,
         "tuning": tuning,
         "serving": serving,
+        "descent": descent,
         "early_exit": early,
         "stages_ms": stages,
         "stats": {k: int(v) for k, v in st.items()},
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_descent(args, dev):
+    """The differentiation workload: 64 clouds of 2048 uniform points in
+    [0,1)^3, loss = sum of squared finite deaths, SGD (lr 1e-2) on the
+    coordinates.  Time per step (forward, backward, update) with one call
+    per cloud and with the clouds spread over 8 streams (ph0.Batch)."""
+    import torch
+
+    from paper_2203_02527_gb300 import ph0
+    xs = [inputs.uniform(2048, 3, seed=1000 + c) for c in range(64)]
+    m = 2048 * 2047 // 2
+    out = {"clouds": 64, "n": 2048, "d": 3, "edges_per_step": 64 * m}
+    for mode in ("one_at_a_time", "batched"):
+        pts = [torch.from_numpy(x).to(dev).requires_grad_(True) for x in xs]
+        opt = torch.optim.SGD(pts, lr=1e-2)
+        batch = ph0.Batch([x.shape for x in xs], streams=8, device=dev)
+        ws = batch.workspaces[0]
+        losses, times = [], []
+        for step in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            opt.zero_grad()
+            if mode == "batched":
+                deaths = batch.death_values(pts)
+            else:
+                deaths = [ph0.death_values(p, ws) for p in pts]
+            total = sum((dv ** 2).sum() for dv in deaths)
+            total.backward()
+            opt.step()
+            losses.append(float(total.detach()))  # reads the loss back: a sync
+            if step >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        ms = 1e3 * float(np.mean(times))
+        out[mode] = {"ms_per_step": ms, "clouds_per_s": 64 / (ms * 1e-3), "edges_per_s": 64 * m / (ms * 1e-3),
+                     "loss_first": losses[0], "loss_last": losses[-1]}
+        del batch
+        torch.cuda.empty_cache()
+    out["timing"] = "host clock around each step (the loss is read back every step)"
+    return out
 
 
 def time_early_configs(args, dev, flush):
@@ -522,6 +564,7 @@ def main():
                     help="also time the single-threaded oracle on the whole cloud (minutes, ~40 GB of host memory)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
     ap.add_argument("--no-early", action="store_true", help="skip timing the early-terminating path")
+    ap.add_argument("--no-descent", action="store_true", help="skip the 64-cloud gradient-descent timing")
     ap.add_argument("--serve-clouds", type=int, default=10000,
                     help="clouds in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-budget", type=int, default=64, help="serving device arena, GiB")

@@ -84,6 +84,7 @@ def _load():
                 "ph0o_barcodes": [vp, i64, i32, i64, vp, vp, vp, vp],
                 "ph0o_death_gradient": [vp, i64, i32, i64, vp, vp, vp, i64, vp],
                 "ph0o_barcodes_below": [vp, i64, i32, i64, ctypes.c_double, vp, vp, vp, vp],
+                "ph0o_h1": [vp, i64, i32, i64, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -221,6 +222,29 @@ def barcodes_below(x, t_max: float):
     _check(_load().ph0o_barcodes_below(_ptr(x), n, d, d, float(t_max), _ptr(bars), ctypes.byref(nb),
                                        ctypes.byref(kept), ctypes.byref(nd)), "barcodes_below")
     return bars[: nb.value].copy(), int(kept.value), int(nd.value)
+
+
+H1_DTYPE = np.dtype([
+    ("eu", np.int32), ("ev", np.int32), ("tu", np.int32), ("tv", np.int32), ("tw", np.int32),
+    ("birth_a", np.uint32), ("death_a", np.uint32), ("pad", np.int32),
+    ("birth_order", np.int64), ("death_order", np.int64), ("death_rank", np.int64),
+    ("birth_sq", np.float64), ("death_sq", np.float64),
+])
+
+
+def h1(x):
+    """First-homology bars of the Vietoris-Rips 2-skeleton (the extension the
+    paper names): (bars in triangle order, triangle count).  Each bar pairs a
+    positive edge (birth) with the triangle whose reduced column has that
+    edge as its low (death); zero-length bars included."""
+    x = _points(x)
+    n, d = x.shape
+    m = n * (n - 1) // 2
+    bars = np.zeros(max(m, 1), H1_DTYPE)
+    nb = ctypes.c_int64(0)
+    nt = ctypes.c_int64(0)
+    _check(_load().ph0o_h1(_ptr(x), n, d, d, _ptr(bars), ctypes.byref(nb), ctypes.byref(nt)), "h1")
+    return bars[: nb.value].copy(), int(nt.value)
 
 
 def death_gradient(x64, bar_u, bar_v, dl_ddeath):

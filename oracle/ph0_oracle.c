@@ -527,3 +527,164 @@ done:
     free(r); free(us); free(vs); free(low); free(d2s); free(a); free(pivot_of);
     return rc;
 }
+
+/* --------------------------------------------------------------------------
+ * First homology (the extension the paper names in Sec. 1 and Sec. 4.2): the
+ * Vietoris-Rips 2-skeleton adds a triangle on three points once its three
+ * edges are present (Sec. 1, the recursive rule), i.e. at the largest of its
+ * edges' distances, its diameter.  The boundary matrix has a row per edge (in
+ * the sorted edge order of step 2) and a column per triangle, with the
+ * triangle's three edges set; entries t^a over F2[t] reduce like the F2
+ * supports (as in dimension 0).  Triangles are ordered by the position of
+ * their diameter edge in the edge order, then (u, v, w) lexicographically.
+ * The columns are reduced left to right with low = largest row; each nonzero
+ * reduced column pairs its low edge (a positive edge: it closes a cycle)
+ * with the triangle, the bar (a(edge), a(diameter of the triangle)).  The
+ * 2-skeleton of the full simplex has no first homology, so every positive
+ * edge is paired: n(n-1)/2 - (n-1) bars, zero-length ones included.
+ * Outputs in column order; n <= 2000 (triangle counts below 2^31).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t eu, ev;             /* birth edge, eu < ev                          */
+    int32_t tu, tv, tw;         /* death triangle, tu < tv < tw                 */
+    uint32_t birth_a, death_a;  /* 1-based indices in D                         */
+    int32_t pad;
+    int64_t birth_order;        /* position of the birth edge in the edge order */
+    int64_t death_order;        /* position of the triangle's diameter edge     */
+    int64_t death_rank;         /* position of the triangle in triangle order   */
+    double birth_sq, death_sq;  /* squared distances                            */
+} ph0o_h1bar;
+
+typedef struct {
+    int64_t diam;
+    int32_t u, v, w, pad;
+} tri_rec;
+
+static int cmp_tri(const void *pa, const void *pb)
+{
+    const tri_rec *a = (const tri_rec *)pa, *b = (const tri_rec *)pb;
+    if (a->diam != b->diam) return a->diam < b->diam ? -1 : 1;
+    if (a->u != b->u) return a->u < b->u ? -1 : 1;
+    if (a->v != b->v) return a->v < b->v ? -1 : 1;
+    if (a->w != b->w) return a->w < b->w ? -1 : 1;
+    return 0;
+}
+
+static int cmp_i64(const void *pa, const void *pb)
+{
+    const int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int ph0o_h1(const float *x, int64_t n, int32_t d, int64_t ld, ph0o_h1bar *bars,
+            int64_t *n_bars, int64_t *n_triangles)
+{
+    int64_t m, T, nb = 0;
+    int32_t *u = 0, *v = 0;
+    int64_t *order = 0, *pos_of = 0, *pivot_of = 0;
+    double *d2 = 0, *d2s = 0;
+    uint32_t *a = 0;
+    tri_rec *tri = 0;
+    column *reduced = 0;   /* reduced column of the pivot owner, by low row */
+    column work = {0, 0, 0}, tmp = {0, 0, 0};
+    int64_t n_distinct = 0;
+    int rc = OK;
+    if (n < 1 || d < 1 || ld < d || n > 2000) return ERR_ARG;
+    m = n * (n - 1) / 2;
+    T = n * (n - 1) * (n - 2) / 6;
+    u = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+    v = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+    order = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    pos_of = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    pivot_of = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    d2 = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    d2s = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    a = (uint32_t *)malloc((size_t)(m + 1) * sizeof(uint32_t));
+    tri = (tri_rec *)malloc((size_t)(T + 1) * sizeof(tri_rec));
+    reduced = (column *)calloc((size_t)(m + 1), sizeof(column));
+    if (!u || !v || !order || !pos_of || !pivot_of || !d2 || !d2s || !a || !tri || !reduced) {
+        rc = ERR_MEM;
+        goto done;
+    }
+    /* steps 1-3 of dimension 0: edge order, positions, a */
+    ph0o_edge_endpoints(n, u, v);
+    if ((rc = ph0o_distances(x, n, d, ld, d2)) != OK) goto done;
+    if ((rc = ph0o_sort_edges(d2, u, v, m, order)) != OK) goto done;
+    for (int64_t p = 0; p < m; ++p) {
+        pos_of[order[p]] = p;
+        d2s[p] = d2[order[p]];
+        pivot_of[p] = -1;
+    }
+    if ((rc = ph0o_dedupe(d2s, m, a, &n_distinct)) != OK) goto done;
+    /* triangles and their diameters, in triangle order */
+    {
+        int64_t k = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = i + 1; j < n; ++j)
+                for (int64_t l = j + 1; l < n; ++l) {
+                    const int64_t pij = pos_of[i * (2 * n - i - 1) / 2 + (j - i - 1)];
+                    const int64_t pil = pos_of[i * (2 * n - i - 1) / 2 + (l - i - 1)];
+                    const int64_t pjl = pos_of[j * (2 * n - j - 1) / 2 + (l - j - 1)];
+                    int64_t mx = pij > pil ? pij : pil;
+                    mx = mx > pjl ? mx : pjl;
+                    tri[k].diam = mx;
+                    tri[k].u = (int32_t)i;
+                    tri[k].v = (int32_t)j;
+                    tri[k].w = (int32_t)l;
+                    tri[k].pad = 0;
+                    ++k;
+                }
+        if (T > 0) qsort(tri, (size_t)T, sizeof(tri_rec), cmp_tri);
+    }
+    /* column reduction, left to right, no early exit */
+    for (int64_t j = 0; j < T; ++j) {
+        const int64_t i0 = tri[j].u, j0 = tri[j].v, l0 = tri[j].w;
+        int64_t e3[3];
+        e3[0] = pos_of[i0 * (2 * n - i0 - 1) / 2 + (j0 - i0 - 1)];
+        e3[1] = pos_of[i0 * (2 * n - i0 - 1) / 2 + (l0 - i0 - 1)];
+        e3[2] = pos_of[j0 * (2 * n - j0 - 1) / 2 + (l0 - j0 - 1)];
+        qsort(e3, 3, sizeof(int64_t), cmp_i64);
+        if (col_reserve(&work, 3) != OK) { rc = ERR_MEM; goto done; }
+        for (int q = 0; q < 3; ++q) work.rows[q] = (int32_t)e3[q];
+        work.len = 3;
+        while (work.len > 0) {
+            const int32_t L = work.rows[work.len - 1];
+            if (pivot_of[L] < 0) {
+                const int64_t pe = L;
+                pivot_of[L] = j;
+                if (col_reserve(&reduced[L], work.len) != OK) { rc = ERR_MEM; goto done; }
+                memcpy(reduced[L].rows, work.rows, (size_t)work.len * sizeof(int32_t));
+                reduced[L].len = work.len;
+                if (nb >= m) { rc = ERR_STATE; goto done; }
+                bars[nb].eu = u[order[pe]];
+                bars[nb].ev = v[order[pe]];
+                bars[nb].tu = tri[j].u;
+                bars[nb].tv = tri[j].v;
+                bars[nb].tw = tri[j].w;
+                bars[nb].pad = 0;
+                bars[nb].birth_a = a[pe];
+                bars[nb].death_a = a[tri[j].diam];
+                bars[nb].birth_order = pe;
+                bars[nb].death_order = tri[j].diam;
+                bars[nb].death_rank = j;
+                bars[nb].birth_sq = d2s[pe];
+                bars[nb].death_sq = d2s[tri[j].diam];
+                ++nb;
+                break;
+            }
+            if (col_symdiff(&work, &reduced[L], &tmp) != OK) { rc = ERR_MEM; goto done; }
+            { column t = work; work = tmp; tmp = t; }
+        }
+    }
+    *n_bars = nb;
+    *n_triangles = T;
+done:
+    if (reduced) {
+        for (int64_t r = 0; r < m; ++r) free(reduced[r].rows);
+        free(reduced);
+    }
+    free(work.rows); free(tmp.rows);
+    free(u); free(v); free(order); free(pos_of); free(pivot_of);
+    free(d2); free(d2s); free(a); free(tri);
+    return rc;
+}

@@ -282,3 +282,59 @@ class DeathValues(torch.autograd.Function):
 def death_values(pts: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor:
     """Finite death values (float64 [N-1], filtration order), differentiable."""
     return DeathValues.apply(pts, ws)
+
+
+class DeathValuesBatch(torch.autograd.Function):
+    """DeathValues over many clouds at once: every cloud's forward path and
+    backward kernel is queued on one of several CUDA streams, so the clouds'
+    kernels overlap on the GPU; the statuses are read once all are queued."""
+
+    @staticmethod
+    def forward(ctx, workspaces, streams, *pts):
+        cur = torch.cuda.current_stream()
+        bars = []
+        for i, p in enumerate(pts):
+            s = streams[i % len(streams)]
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                bars.append(barcodes(p, workspaces[i], sync=False))
+        for i, ws in enumerate(workspaces[:len(pts)]):
+            with torch.cuda.stream(streams[i % len(streams)]):
+                finish(ws)  # waits for that stream; raises on a device error
+        for s in streams:
+            cur.wait_stream(s)
+        out = [b.death for b in bars]  # on the current stream, after every cloud finished
+        ctx.save_for_backward(*pts)
+        ctx.bars, ctx.workspaces, ctx.streams = bars, workspaces, streams
+        return tuple(out)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        pts = ctx.saved_tensors
+        cur = torch.cuda.current_stream()
+        out = []
+        for i, (p, g) in enumerate(zip(pts, grads)):
+            s = ctx.streams[i % len(ctx.streams)]
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                gp = backward(p, ctx.bars[i], g.contiguous(), ctx.workspaces[i])
+            gp.record_stream(cur)  # made on s, used on the current stream
+            out.append(gp)
+        for s in ctx.streams:
+            cur.wait_stream(s)
+        return (None, None, *out)
+
+
+class Batch:
+    """Workspaces and streams for death_values over a fixed set of cloud
+    shapes (one workspace per cloud, so that clouds on different streams
+    never share one)."""
+
+    def __init__(self, shapes, streams: int = 8, device=None):
+        self.workspaces = [Workspace(n, d, device) for n, d in shapes]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+
+    def death_values(self, pts_list):
+        """Finite death values of every cloud (a tuple of float64 tensors),
+        differentiable with respect to each cloud's points."""
+        return DeathValuesBatch.apply(self.workspaces, self.streams, *pts_list)

@@ -97,3 +97,20 @@ def test_gradient_descent_64_clouds():
     ob = oracle.barcodes(x)[0]
     ref = oracle.death_gradient(x.astype(np.float64), ob["u"], ob["v"], 2.0 * ob["death"])
     np.testing.assert_allclose(p.grad.cpu().numpy(), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+
+
+def test_batched_death_values_equal_one_at_a_time():
+    """The batched form (clouds on several streams) gives the same deaths and
+    gradients as one call per cloud."""
+    ph0 = _ph0()
+    xs = [inputs.uniform(700 + 37 * c, 3, seed=2000 + c) for c in range(12)]
+    batch = ph0.Batch([x.shape for x in xs], streams=4)
+    pts = [torch.from_numpy(x).cuda().requires_grad_(True) for x in xs]
+    deaths = batch.death_values(pts)
+    sum((dv ** 2).sum() for dv in deaths).backward()
+    for x, p, dv in zip(xs, pts, deaths):
+        q = torch.from_numpy(x).cuda().requires_grad_(True)
+        one = ph0.death_values(q)
+        assert torch.equal(one, dv)
+        (one ** 2).sum().backward()
+        np.testing.assert_allclose(p.grad.cpu().numpy(), q.grad.cpu().numpy(), rtol=1e-6, atol=1e-9)
