@@ -35,10 +35,11 @@ from paper_2203_02527_gb300.replicas import job_throughput, max_over_ranks, repl
 WORKLOAD = "circles32768"
 # DRAM bytes per edge (dram__bytes_read.sum + dram__bytes_write.sum over the
 # launch, divided by its edges) of the kernels of the distance+sort phase,
-# from one ncu capture on the 8192-point circles cloud
+# from one ncu capture per kernel on the 8192-point circles cloud
 # (profiles/kernels_circles8192.md), scaled by edges to the benchmark cloud:
-# the distance kernel, one radix pass (mean of the passes), the fix-up.
-PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 24.51, "k_sort_fixup": 8.16}
+# the distance kernel, one radix pass (mean of the captured slots 4, 5 and
+# the top pass), the fix-up.
+PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 24.64, "k_sort_fixup": 8.18}
 ONESWEEP_TRAFFIC_PER_EDGE = PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
 # the algorithmic floor of the phase (steps 1-3): write the records (12 B),
 # read and write them once to sort (24 B), read the keys and write a (12 B)
@@ -299,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
     roof_sort = {"kernel": "k_onesweep", "bound": "hbm", "achieved": achieved, "peak": hbm,
                  "unit": "GB/s", "frac": achieved / hbm,
                  "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
-                 "traffic_source": "ncu on the 8192-point cloud, scaled by edges",
+                 "traffic_source": "ncu on the 8192-point cloud (slots 4-6), scaled by edges",
                  "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src,
                  "launches": len(ran), "ms_per_launch": per_pass_ms}
     # the distance kernel: its binding unit is the binary64 adder, which takes

@@ -288,6 +288,49 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
 int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                          ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *stream);
 
+/* ---- first homology (the extension the paper names, Sec. 1 and Sec. 4.2) ----
+ *
+ * The Vietoris-Rips 2-skeleton adds a triangle once its three edges are
+ * present (Sec. 1, the recursive rule), at its diameter.  The edge-by-
+ * triangle boundary matrix (entries t^a over F2[t], reducing like their F2
+ * supports) is reduced left to right, triangles ordered by the position of
+ * their diameter edge in the sorted edge order, then (u, v, w); each nonzero
+ * reduced column pairs its low edge (a positive edge: one that closes a
+ * cycle) with its triangle, the bar (a(edge), a(diameter)).  Every positive
+ * edge is paired (the full simplex has no first homology): n(n-1)/2 - (n-1)
+ * bars, zero-length ones included, in triangle order.  72 bytes. */
+typedef struct {
+    int32_t eu, ev;             /* birth edge, eu < ev                               */
+    int32_t tu, tv, tw;         /* death triangle, tu < tv < tw                      */
+    uint32_t birth_a, death_a;  /* 1-based indices in D of the birth edge and of the
+                                   triangle's diameter edge                         */
+    int32_t _pad;
+    int64_t birth_order;        /* position of the birth edge in the sorted edge list */
+    int64_t death_order;        /* position of the triangle's diameter edge          */
+    int64_t death_rank;         /* position of the triangle in the triangle order    */
+    double birth_sq, death_sq;  /* squared distances                                 */
+} ph0_h1bar;
+
+typedef struct {
+    int64_t n_bars;             /* bars written: n(n-1)/2 - (n-1)                    */
+    int64_t n_triangles;        /* n(n-1)(n-2)/6                                     */
+    int64_t pool_entries;       /* stored entries of reduced, non-apparent columns   */
+    int32_t rounds;             /* ordering rounds over all windows                  */
+    int32_t max_column;         /* longest column met under reduction                */
+} ph0_h1_stats;
+
+/* Workspace bytes of ph0_h1() for n points in dimension d (0 on invalid sizes;
+ * 3 <= n needs triangles, n <= 1024). */
+size_t ph0_h1_workspace_bytes(int64_t n, int32_t d);
+
+/* First-homology bars of the cloud (steps 1-3 of the dimension-0 path for the
+ * edge order and a, then the triangles).  bars_dev: ph0_h1bar[n(n-1)/2 - (n-1)]
+ * (none for n <= 2).  1 <= n <= 1024.  Synchronous: waits for `stream` and
+ * returns the device status; PH0_ETOOBIG also when a column under reduction
+ * would exceed 256 entries.  stats may be NULL. */
+int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *bars_dev, void *ws,
+           size_t ws_bytes, void *stream, ph0_h1_stats *stats);
+
 /* ---- serving: a context that admits clouds as they arrive ----
  *
  * The paper computes one cloud at a time (Sec. 3.1, Sec. 4.1); this context

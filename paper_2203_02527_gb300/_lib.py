@@ -91,6 +91,24 @@ class Options(ctypes.Structure):
     ]
 
 
+H1_DTYPE = np.dtype([
+    ("eu", np.int32), ("ev", np.int32), ("tu", np.int32), ("tv", np.int32), ("tw", np.int32),
+    ("birth_a", np.uint32), ("death_a", np.uint32), ("pad", np.int32),
+    ("birth_order", np.int64), ("death_order", np.int64), ("death_rank", np.int64),
+    ("birth_sq", np.float64), ("death_sq", np.float64),
+])
+H1_BAR_BYTES = H1_DTYPE.itemsize  # 72
+
+
+class H1Stats(ctypes.Structure):
+    _fields_ = [("n_bars", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("pool_entries", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("max_column", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class InfBar(ctypes.Structure):
     _fields_ = [("vertex", ctypes.c_int32), ("_pad", ctypes.c_int32),
                 ("birth", ctypes.c_double), ("death", ctypes.c_double)]
@@ -140,6 +158,8 @@ SIGNATURES = {
     "ph0_reduce": (ctypes.c_int, [_I64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "ph0_barcodes_backward": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _I64, _VP, _VP,
                                              _VP, _SZ, _VP]),
+    "ph0_h1_workspace_bytes": (_SZ, [_I64, _I32]),
+    "ph0_h1": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _SZ, _VP, ctypes.POINTER(H1Stats)]),
 }
 
 

@@ -81,40 +81,6 @@ __global__ void k_reduce_init(ReduceArgs A) {
     }
 }
 
-// Grid-wide barrier with a bounded wait (spin_limit polls).  Returns false
-// (in every thread of the CTA) if the kernel must stop.
-__device__ bool grid_barrier(Header *h, int *s_ok, uint32_t spin_limit) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const uint32_t nblocks = gridDim.x;
-        const uint32_t gen = ld_volatile(&h->bar_gen);
-        __threadfence();
-        const uint32_t arrived = atomicAdd(&h->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&h->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&h->bar_gen, 1u);
-        } else {
-            uint32_t spins = 0;
-            while (ld_volatile(&h->bar_gen) == gen) {
-                if (ld_volatile(&h->abort)) { ok = 0; break; }
-                if (++spins > spin_limit) {
-                    set_status(h, PH0_ETIMEOUT);
-                    atomicExch(&h->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 16) __nanosleep(32);
-            }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
-
 __device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t r) {
     for (;;) {
         const uint32_t p = __ldcg(parent + r);

@@ -56,6 +56,10 @@ cudaError_t launch_backward(const float *pts, int64_t n, int32_t d, int64_t ld, 
 
 cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s);
 cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s);
+cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, const uint64_t *ek1,
+                   const uint32_t *ev0, const uint32_t *ev1, const Header *esort, const uint32_t *cpref,
+                   Header *h, ph0_h1bar *bars, cudaStream_t s);
+cudaError_t h1_counters(const void *ws, const H1Layout &H, uint64_t out[5]);
 cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
@@ -644,6 +648,52 @@ int ph0_barcodes_backward(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return cuda_status(launch_backward(pts_dev, n, d, ld, bars_dev, n_bars, dl_ddeath_dev, grad_dev,
                                        at<double>(ws, L.grad), s));
+}
+
+size_t ph0_h1_workspace_bytes(int64_t n, int32_t d) {
+    if (check_sizes(n, d, d, kH1MaxN) != PH0_OK) return 0;
+    const Layout L(n, d);
+    return H1Layout(n, L.total).total;
+}
+
+int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *bars_dev, void *ws,
+           size_t ws_bytes, void *stream, ph0_h1_stats *stats) {
+    int rc = check_sizes(n, d, ld, kH1MaxN);
+    if (rc != PH0_OK) return rc;
+    const int64_t m = n_edges(n), nbars = m - (n - 1);
+    if (!pts_dev || !ws || (nbars > 0 && !bars_dev)) return PH0_EINVAL;
+    if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8)) return PH0_EINVAL;
+    const Layout L(n, d);
+    const H1Layout H(n, L.total);
+    if (ws_bytes < H.total) return PH0_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Tune t(nullptr, n);
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
+    // steps 1-3 of dimension 0: the edge order and the de-duplication
+    cudaError_t e = begin_call(ws, L, s, t.top_bits);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
+    if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
+    if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
+    if (e == cudaSuccess && nbars > 0) e = run_h1(ws, H, n, k0, k1, v0, v1, h, cpref, h, bars_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    uint64_t cnt[5] = {0, 0, 0, 0, 0};
+    int32_t status = PH0_OK;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nbars > 0) e = h1_counters(ws, H, cnt);
+    if (e != cudaSuccess) return PH0_ECUDA;
+    if (status == PH0_OK && cnt[4] != 0) status = int32_t(cnt[4]);  // the triangle sort's status
+    if (status == PH0_OK && nbars > 0 && int64_t(cnt[0]) != nbars) status = PH0_EINTERNAL;
+    if (stats) {
+        stats->n_bars = nbars > 0 ? int64_t(cnt[0]) : 0;
+        stats->n_triangles = H.T;
+        stats->pool_entries = int64_t(cnt[1]);
+        stats->rounds = int32_t(cnt[2]);
+        stats->max_column = int32_t(cnt[3]);
+    }
+    return status;
 }
 
 }  // extern "C"

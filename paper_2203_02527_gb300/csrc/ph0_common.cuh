@@ -189,6 +189,53 @@ struct Layout {
     }
 };
 
+// First homology (k_h1.cu): at most kH1MaxN points (vertex ids packed in
+// 10 bits per triangle), kH1Window triangles reduced per window, kH1Cap
+// entries per column under reduction.
+constexpr int64_t kH1MaxN = 1024;
+constexpr int64_t kH1Window = int64_t(1) << 18;
+constexpr int kH1Cap = 256;
+constexpr int kH1ChunkTris = 4096;   // triangles per CTA in the compaction
+
+// The first-homology regions of a workspace, after the dimension-0 layout.
+struct H1Layout {
+    int64_t T, ttiles, W, pool_cap, chunks;
+    size_t thdr, cnt, aof, posof, tkey[2], tval[2], tlook[2], own_tri, own_off, own_len, pair_low, slots,
+        slen, pool, ccount, total;
+    H1Layout(int64_t n, size_t base) {
+        const int64_t m = n_edges(n);
+        T = n * (n - 1) * (n - 2) / 6;
+        ttiles = (T + kSortTile - 1) / kSortTile;
+        W = T < kH1Window ? T : kH1Window;
+        pool_cap = (int64_t(1) << 20) + 16 * m;
+        chunks = (T + kH1ChunkTris - 1) / kH1ChunkTris;
+        size_t off = base;
+        auto take = [&](size_t bytes) {
+            size_t o = off;
+            off = align_up(off + bytes, 256);
+            return o;
+        };
+        thdr = take(kHeaderBytes);
+        cnt = take(256);
+        aof = take(4 * size_t(m + 1));
+        posof = take(4 * size_t(m + 1));
+        for (int b = 0; b < 2; ++b) {
+            tkey[b] = take(8 * size_t(T + 1));
+            tval[b] = take(4 * size_t(T + 1));
+            tlook[b] = take(8 * size_t(ttiles) * kMaxRadix);
+        }
+        own_tri = take(4 * size_t(m + 1));
+        own_off = take(4 * size_t(m + 1));
+        own_len = take(4 * size_t(m + 1));
+        pair_low = take(4 * size_t(T + 1));
+        slots = take(4 * size_t(W) * 2 * kH1Cap);
+        slen = take(4 * size_t(W + 1));
+        pool = take(4 * size_t(pool_cap));
+        ccount = take(4 * size_t(chunks + 1));
+        total = off;
+    }
+};
+
 // Arguments of the persistent reduction kernel (steps 4-5).
 struct ReduceArgs {
     int64_t n, m;
@@ -240,6 +287,40 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t *p) {
 }
 __device__ __forceinline__ void st_volatile(uint64_t *p, uint64_t v) {
     *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+
+// Grid-wide barrier with a bounded wait (spin_limit polls).  Returns false
+// (in every thread of the CTA) if the kernel must stop.
+__device__ __forceinline__ bool grid_barrier(Header *h, int *s_ok, uint32_t spin_limit) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t nblocks = gridDim.x;
+        const uint32_t gen = ld_volatile(&h->bar_gen);
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&h->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&h->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&h->bar_gen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (ld_volatile(&h->bar_gen) == gen) {
+                if (ld_volatile(&h->abort)) { ok = 0; break; }
+                if (++spins > spin_limit) {
+                    set_status(h, PH0_ETIMEOUT);
+                    atomicExch(&h->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 16) __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 // Edge index of (u, v), u < v, in lexicographic order.

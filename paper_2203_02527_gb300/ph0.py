@@ -166,6 +166,24 @@ def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torc
     return Bars(bars, n, None, inf), prof.as_dict()
 
 
+def h1(pts: torch.Tensor):
+    """First-homology bars of the Vietoris-Rips 2-skeleton (ph0_h1; waits
+    for the GPU): (structured host array in triangle order, stats).  Every
+    positive edge is paired, zero-length bars included; n <= 1024."""
+    pts, n, d, ld = _points(pts)
+    lib = _lib.load()
+    nbytes = int(lib.ph0_h1_workspace_bytes(n, d))
+    if nbytes == 0:
+        raise _lib.Ph0Error(3, f"ph0_h1_workspace_bytes(n={n}, d={d})")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=pts.device)
+    nb = max(n * (n - 1) // 2 - (n - 1), 0)
+    bars = torch.empty((max(nb, 1), _lib.H1_BAR_BYTES), dtype=torch.uint8, device=pts.device)
+    st = _lib.H1Stats()
+    check(lib.ph0_h1(_ptr(pts), n, d, ld, _ptr(bars), _ptr(ws), nbytes, _stream(), ctypes.byref(st)), "ph0_h1")
+    out = bars[:nb].cpu().numpy().reshape(-1).view(_lib.H1_DTYPE).copy()
+    return out, st.as_dict()
+
+
 def trace_windows(ws: Workspace, n: int, d: int, max_windows: int = 256):
     """Per-window records of the last reduction on `ws` (tracing aid)."""
     out = np.zeros((max_windows, 12), np.uint64)

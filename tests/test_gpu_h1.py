@@ -1,0 +1,53 @@
+"""First homology on the GPU (ph0_h1: the edge-by-triangle matrix of the
+Vietoris-Rips 2-skeleton reduced with apparent pairs and ordered rounds)
+against the oracle's literal left-to-right reduction, every field of every
+bar, bit for bit: the birth edge, the death triangle, the indices a of both,
+their positions in the edge and triangle orders, and the squared distances."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02527_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CLOUDS = {
+    "square": lambda: np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32),
+    "uniform2d_64": lambda: inputs.uniform(64, 2, seed=31),
+    "uniform2d_200": lambda: inputs.uniform(200, 2, seed=32),
+    "uniform3d_150": lambda: inputs.uniform(150, 3, seed=33),
+    "mixture_d8": lambda: inputs.gaussian_mixture(120, 8, k=4, sigma=0.3, seed=34),
+    "circles_d4": lambda: inputs.noisy_circles(40, 3, 4, noise=0.05, seed=35),
+    "lattice_ties": lambda: inputs.lattice(9, 2),
+    "duplicates": lambda: inputs.with_duplicates(90, 2, 30, seed=36),
+    "negative_zero": lambda: inputs.negative_zero_mix(60, 3, seed=37),
+}
+
+
+def _check(x):
+    from paper_2203_02527_gb300 import ph0
+    want, ntri = oracle.h1(x)
+    got, st = ph0.h1(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    assert st["n_triangles"] == ntri and st["n_bars"] == len(want)
+    for f in ("eu", "ev", "tu", "tv", "tw", "birth_a", "death_a", "birth_order", "death_order", "death_rank"):
+        np.testing.assert_array_equal(got[f], want[f], err_msg=f)
+    for f in ("birth_sq", "death_sq"):
+        np.testing.assert_array_equal(got[f].view(np.uint64), want[f].view(np.uint64), err_msg=f)
+    return st
+
+
+@pytest.mark.parametrize("name", sorted(CLOUDS))
+def test_h1_equals_oracle(name):
+    _check(CLOUDS[name]())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 33])
+def test_h1_small_and_ragged(n):
+    _check(inputs.uniform(n, 2, seed=300 + n))
+
+
+def test_h1_many_windows():
+    # 300 points: 4.5M triangles, 18 windows of the round kernel
+    st = _check(inputs.uniform(300, 2, seed=38))
+    assert st["rounds"] >= 18
