@@ -366,6 +366,12 @@ def run_ours(args, rank, world, local_rank):
                         "sample": "the whole cloud", "bars_identical_to_gpu": same}
     serving = run_serving(args, dev) if (args.serve_clouds > 0 and world == 1) else None
     descent = run_descent(args, dev) if (world == 1 and not args.no_descent) else None
+    h1 = None
+    if world == 1 and not args.no_h1:
+        try:
+            h1 = run_h1(args, dev)
+        except Exception as exc:  # reported in the line; the other measurements stand
+            h1 = {"error": str(exc)}
     line = {
         "metric": METRIC, "value": job_throughput(m, world, ms), "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -389,6 +395,7 @@ def run_ours(args, rank, world, local_rank):
         "tuning": tuning,
         "serving": serving,
         "descent": descent,
+        "h1": h1,
         "early_exit": early,
         "stages_ms": stages,
         "stats": {k: int(v) for k, v in st.items()},
@@ -434,6 +441,41 @@ def run_descent(args, dev):
         del batch
         torch.cuda.empty_cache()
     out["timing"] = "host clock around each step (the loss is read back every step)"
+    return out
+
+
+def run_h1(args, dev):
+    """First homology (ph0_h1) on uniform points in the unit square, the
+    paper's workload (at 256 points and at its largest N, 700): host clock around the
+    synchronous call; the oracle's literal reduction timed beside it on one
+    core where it finishes in seconds."""
+    import torch
+
+    from paper_2203_02527_gb300 import ph0
+    out = {}
+    for n in (256, 700):
+        x = inputs.uniform(n, 2, seed=20260109 + n)
+        pts = torch.from_numpy(x).to(dev)
+        times = []
+        for i in range(1 + min(args.steps, 3)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bars, st = ph0.h1(pts)
+            if i:
+                times.append(time.perf_counter() - t0)
+        ms = 1e3 * float(np.mean(times))
+        out[f"uniform{n}_2d"] = {"ms": ms, "triangles": st["n_triangles"], "bars": st["n_bars"],
+                                 "triangles_per_s": st["n_triangles"] / (ms * 1e-3), "rounds": st["rounds"],
+                                 "max_column": st["max_column"], "pool_entries": st["pool_entries"],
+                                 "nonzero_bars": int((bars["death_sq"] > bars["birth_sq"]).sum())}
+    if not args.no_cpu_baseline:
+        import oracle
+        x = inputs.uniform(256, 2, seed=20260109 + 256)
+        t0 = time.perf_counter()
+        oracle.h1(x)
+        dt = time.perf_counter() - t0
+        out["oracle_uniform256_2d"] = {"ms": 1e3 * dt, "cores": 1, "kind": "oracle"}
+    out["timing"] = "host clock around the synchronous call (workspace allocated inside)"
     return out
 
 
@@ -566,6 +608,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
     ap.add_argument("--no-early", action="store_true", help="skip timing the early-terminating path")
     ap.add_argument("--no-descent", action="store_true", help="skip the 64-cloud gradient-descent timing")
+    ap.add_argument("--no-h1", action="store_true", help="skip the first-homology timing")
     ap.add_argument("--serve-clouds", type=int, default=10000,
                     help="clouds in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-budget", type=int, default=64, help="serving device arena, GiB")

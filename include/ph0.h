@@ -327,7 +327,7 @@ size_t ph0_h1_workspace_bytes(int64_t n, int32_t d);
  * edge order and a, then the triangles).  bars_dev: ph0_h1bar[n(n-1)/2 - (n-1)]
  * (none for n <= 2).  1 <= n <= 1024.  Synchronous: waits for `stream` and
  * returns the device status; PH0_ETOOBIG also when a column under reduction
- * would exceed 256 entries.  stats may be NULL. */
+ * would exceed 512 entries.  stats may be NULL. */
 int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *bars_dev, void *ws,
            size_t ws_bytes, void *stream, ph0_h1_stats *stats);
 

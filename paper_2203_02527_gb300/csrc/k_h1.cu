@@ -32,8 +32,8 @@
 //   5. the paired triangles are compacted in triangle order into the bars.
 // Columns under reduction live in fixed slots of kH1Cap entries; the final
 // columns of non-apparent owners in a pool.  A column that outgrows its slot,
-// or a full pool, stops the kernel with PH0_ETOOBIG (never seen below
-// n = 1024 on the tested clouds, whose columns stay under 64 entries).
+// or a full pool, stops the kernel with PH0_ETOOBIG (uniform points in the
+// plane: columns up to 384 entries at n = 1024, within the 512 of a slot).
 #include "ph0_common.cuh"
 
 namespace ph0 {

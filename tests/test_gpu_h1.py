@@ -51,3 +51,29 @@ def test_h1_many_windows():
     # 300 points: 4.5M triangles, 18 windows of the round kernel
     st = _check(inputs.uniform(300, 2, seed=38))
     assert st["rounds"] >= 18
+
+
+def test_h1_at_the_papers_largest_size_structure():
+    """700 uniform points in the unit square (the paper's largest N; 57M
+    triangles, too many for the oracle's literal reduction in a test): every
+    positive edge dies, the births are exactly the edges that end no class
+    in dimension 0 (from the GPU's own dimension-0 bars, themselves checked
+    against the oracle elsewhere), each death comes at or after its birth,
+    and the indices follow the sorted distances."""
+    from paper_2203_02527_gb300 import ph0
+    x = inputs.uniform(700, 2, seed=39)
+    pts = torch.from_numpy(x).cuda()
+    bars, st = ph0.h1(pts)
+    n, m = 700, 700 * 699 // 2
+    assert st["n_bars"] == len(bars) == m - (n - 1)
+    h0 = ph0.barcodes(pts).numpy()
+    killing = set(zip(h0["u"].tolist(), h0["v"].tolist()))
+    births = set(zip(bars["eu"].tolist(), bars["ev"].tolist()))
+    assert len(births) == len(bars) and births.isdisjoint(killing) and len(births) + len(killing) == m
+    assert (bars["death_order"] >= bars["birth_order"]).all()
+    assert (np.diff(bars["death_rank"]) > 0).all()
+    assert (bars["death_sq"] >= bars["birth_sq"]).all()
+    assert np.array_equal(bars["birth_a"] <= bars["death_a"], np.ones(len(bars), bool))
+    # a agrees with the order of the squared distances
+    o = np.argsort(bars["birth_order"])
+    assert (np.diff(bars["birth_a"][o].astype(np.int64)) >= 0).all()
