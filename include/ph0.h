@@ -180,10 +180,11 @@ int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
  * rounds, because there the rounds' fixed cost (a host wait per round, the
  * histogram and the class pass) exceeds what skipping the sort of the
  * suffix saves (a 4096-point cloud: 3.2 ms in rounds against 1.2 ms whole);
- * above 65535 points the whole path always runs.  Same results either way. */
+ * above 65535 points the whole path always runs.  Same results either way.
+ * stats (may be NULL) receives the counters, as from ph0_finish(). */
 int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
                              ph0_bar *bars_dev, ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes,
-                             void *stream, const ph0_tuning *tuning);
+                             void *stream, const ph0_tuning *tuning, ph0_stats *stats);
 
 /* ph0_barcodes() with explicit tuning (NULL = built-in). */
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld,

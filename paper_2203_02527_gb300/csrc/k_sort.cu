@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
 // Shared memory of one pass: the tile's keys (input, then in sorted order),
 // its values (input, and in sorted order), per-warp digit counts, per-digit
 // destination offsets.
-template <int RADIX>
+template <int RADIX, int THREADS = kSortThreads>
 struct SortSmem {
-    static constexpr int W = kSortThreads / 32;
+    static constexpr int W = THREADS / 32;
     uint64_t keys[kSortTile];          // input keys, then the tile's keys in sorted order
     uint32_t vals_in[kSortTile];       // input values; after the scatter, the top-digit histogram
     uint32_t vals[kSortTile];          // values in sorted order
@@ -288,17 +288,23 @@ __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t
 // buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
 // pass's radix) live in look[p&1], and it clears its tile's words in
 // look[(p+1)&1] for the next pass (whose previous user, pass p-1, is done).
-template <int RADIX, int SLOT, bool ALIGNED, bool PERSIST = false>
-__global__ void __launch_bounds__(kSortThreads, PH0_SORT_MIN_BLOCKS)
+// THREADS: 256 (kSortItems keys each), or 512 with half as many keys each
+// (the same tile): one digit per thread in a 9-bit pass.
+template <int THREADS>
+constexpr int sort_min_blocks() { return THREADS == kSortThreads ? PH0_SORT_MIN_BLOCKS : 2; }
+
+template <int RADIX, int SLOT, bool ALIGNED, bool PERSIST = false, int THREADS = kSortThreads>
+__global__ void __launch_bounds__(THREADS, sort_min_blocks<THREADS>())
 k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
            uint64_t *look0, uint64_t *look1, Header *h) {
-    constexpr int T = kSortThreads, IT = kSortItems, TILE = kSortTile, W = T / 32;
+    constexpr int T = THREADS, IT = kSortTile / THREADS, TILE = kSortTile, W = T / 32;
+    static_assert(IT * T == TILE, "every instance sorts the same tiles");
     static_assert(!(ALIGNED && PERSIST), "the persistent instance loads its tiles by cp.async");
     constexpr int DPT = RADIX / T;  // digits per thread
     static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
     static_assert((TILE & (TILE - 1)) == 0, "tile positions are masked to the tile");
     extern __shared__ __align__(16) unsigned char s_raw[];
-    SortSmem<RADIX> &S = *reinterpret_cast<SortSmem<RADIX> *>(s_raw);
+    SortSmem<RADIX, T> &S = *reinterpret_cast<SortSmem<RADIX, T> *>(s_raw);
 
     const Plan plan = make_plan(h);
     if (SLOT != kClassSlot && SLOT >= plan.passes) return;
@@ -778,8 +784,16 @@ __global__ void __launch_bounds__(256) k_sort_fixup_deferred(uint64_t *keys0, ui
 }
 
 // ------------------------------------------------------------------ host ---
+template <int RADIX, int THREADS = kSortThreads>
+constexpr size_t sort_smem() { return sizeof(SortSmem<RADIX, THREADS>); }
+
+// Threads of the non-persistent instance of a pass slot: the 9-bit top pass
+// takes one digit per thread.
+#ifndef PH0_TOP_THREADS
+#define PH0_TOP_THREADS 256
+#endif
 template <int RADIX>
-constexpr size_t sort_smem() { return sizeof(SortSmem<RADIX>); }
+constexpr int slot_threads() { return RADIX == kMaxRadix ? PH0_TOP_THREADS : kSortThreads; }
 
 int sm_count() {
     int dev = 0, sms = 0;
@@ -810,11 +824,14 @@ cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStre
 
 template <int RADIX, int SLOT>
 static cudaError_t set_attr() {
+    constexpr int TT = slot_threads<RADIX>();
     const int bytes = int(sort_smem<RADIX>());
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
+    const int tbytes = int(sort_smem<RADIX, TT>());
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true, false, TT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tbytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false, false, TT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, tbytes);
     if constexpr (SLOT != kClassSlot)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false, true>,
@@ -853,12 +870,13 @@ static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32
     // tiles arrive by bulk copies only when both buffers' rows are 16-byte aligned
     const bool aligned = ((reinterpret_cast<uintptr_t>(keys0) | reinterpret_cast<uintptr_t>(keys1) |
                            reinterpret_cast<uintptr_t>(vals0) | reinterpret_cast<uintptr_t>(vals1)) & 15u) == 0;
+    constexpr int TT = slot_threads<RADIX>();
     if (aligned)
-        k_onesweep<RADIX, SLOT, true><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1,
-                                                                                     m, look0, look1, h);
+        k_onesweep<RADIX, SLOT, true, false, TT><<<tiles, TT, sort_smem<RADIX, TT>(), s>>>(
+            keys0, keys1, vals0, vals1, m, look0, look1, h);
     else
-        k_onesweep<RADIX, SLOT, false><<<tiles, kSortThreads, sort_smem<RADIX>(), s>>>(keys0, keys1, vals0, vals1,
-                                                                                      m, look0, look1, h);
+        k_onesweep<RADIX, SLOT, false, false, TT><<<tiles, TT, sort_smem<RADIX, TT>(), s>>>(
+            keys0, keys1, vals0, vals1, m, look0, look1, h);
 }
 
 // One pass slot (prepare_sort_kernels() must have run).

@@ -7,6 +7,7 @@
 // state, and the one buffer the caller does not own, is the fixed device
 // array of ph0_barcodes_noalloc (end of this file) with its per-device
 // address cache; that entry point is synchronous.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -294,12 +295,12 @@ int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar
 
 int ph0_barcodes_early(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                        ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
-    return ph0_barcodes_early_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
+    return ph0_barcodes_early_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr, nullptr);
 }
 
 int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                              ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream,
-                             const ph0_tuning *tuning) {
+                             const ph0_tuning *tuning, ph0_stats *stats) {
     int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
@@ -310,7 +311,7 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto whole = [&]() {  // the whole path, then its device status
         const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
-        return r != PH0_OK ? r : ph0_finish(ws, stream, nullptr);
+        return r != PH0_OK ? r : ph0_finish(ws, stream, stats);
     };
     // the whole path: tiny clouds, wide records, and (built-in choice) clouds
     // below kEarlyMinEdges, where the rounds' fixed cost exceeds the saving
@@ -445,7 +446,7 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h->sorted_edges, &P, sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return PH0_ECUDA;
-    return ph0_finish(ws, stream, nullptr);
+    return ph0_finish(ws, stream, stats);
 }
 
 int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld,
@@ -523,8 +524,8 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return PH0_ECUDA;
-    Header hh;
-    e = cudaMemcpy(&hh, ws, sizeof(Header), cudaMemcpyDeviceToHost);
+    Header hh;  // the counters lead the header; its histograms are not read
+    e = cudaMemcpy(&hh, ws, offsetof(Header, part_kmin), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return PH0_ECUDA;
     if (stats) {
         stats->status = hh.status;

@@ -144,9 +144,10 @@ def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None, rounds: bool 
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     inf = _inf_buffer(pts.device)
     t = _lib.Tuning.make(early_rounds=-1 if rounds is None else int(bool(rounds)))
+    st = Stats()
     check(_lib.load().ph0_barcodes_early_tuned(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
-                                               _stream(), ctypes.byref(t)), "ph0_barcodes_early")
-    return Bars(bars, n, finish(ws), inf)
+                                               _stream(), ctypes.byref(t), ctypes.byref(st)), "ph0_barcodes_early")
+    return Bars(bars, n, st.as_dict(), inf)
 
 
 def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torch.Tensor | None = None,
