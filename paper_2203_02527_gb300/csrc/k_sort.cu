@@ -299,7 +299,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
            uint64_t *look0, uint64_t *look1, Header *h) {
     constexpr int T = THREADS, IT = kSortTile / THREADS, TILE = kSortTile, W = T / 32;
     static_assert(IT * T == TILE, "every instance sorts the same tiles");
-    static_assert(!(ALIGNED && PERSIST), "the persistent instance loads its tiles by cp.async");
+
     constexpr int DPT = RADIX / T;  // digits per thread
     static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
     static_assert((TILE & (TILE - 1)) == 0, "tile positions are masked to the tile");
@@ -333,6 +333,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
     // usually return at once), where a CTA takes tiles from the counter until
     // none is left (every tile it waits on belongs to a CTA that is running);
     // the others take one tile per CTA
+    uint32_t phase = 0;  // of the tile mbarrier (a persistent CTA loads tile after tile)
     for (;;) {
         const int64_t tile = S.tile;
         if constexpr (PERSIST) {
@@ -341,11 +342,11 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         const int64_t base = tile * TILE;
         const int valid = int(m - base < TILE ? m - base : TILE);
         // full tiles arrive in shared memory while the histogram scan below runs:
-        // by two bulk copies when their rows are 16-byte aligned, else (the
-        // instances for unaligned buffers, and the persistent one, whose single
-        // mbarrier is never armed) by each thread's asynchronous copies of its
-        // own items; the ragged last tile uses plain loads
-        const bool bulk = !PERSIST && valid == TILE &&
+        // by two bulk copies when their rows are 16-byte aligned (the aligned
+        // instances; a persistent one waits on the mbarrier's next phase each
+        // tile), else by each thread's asynchronous copies of its own items;
+        // the ragged last tile uses plain loads
+        const bool bulk = (ALIGNED || !PERSIST) && valid == TILE &&
                           ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15u) == 0;
         const bool full = ALIGNED ? bulk : valid == TILE;
         if (bulk && tid == 0) {
@@ -403,7 +404,8 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         const int wloc = warp * 32 * IT;  // the warp's first item within the tile
         if (full) {  // each thread reads (and later scatters) only its own items
             if (bulk) {
-                if (!mbar_wait(&S.mbar, 0)) set_status(h, PH0_ETIMEOUT);
+                if (!mbar_wait(&S.mbar, phase)) set_status(h, PH0_ETIMEOUT);
+                phase ^= 1u;
             } else {
                 cp_async_wait_all();
             }
@@ -832,10 +834,14 @@ static cudaError_t set_attr() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false, false, TT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tbytes);
-    if constexpr (SLOT != kClassSlot)
+    if constexpr (SLOT != kClassSlot) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, false, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_onesweep<RADIX, SLOT, true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
     return e;
 }
 
@@ -859,17 +865,24 @@ cudaError_t prepare_sort_kernels() {
 template <int RADIX, int SLOT>
 static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                         int64_t m, uint64_t *look0, uint64_t *look1, Header *h, bool persist, cudaStream_t s) {
-    if constexpr (SLOT != kClassSlot) {
-        if (persist) {
-            const unsigned cap = unsigned(sm_count()) * PH0_SORT_MIN_BLOCKS;
-            k_onesweep<RADIX, SLOT, false, true><<<tiles < cap ? tiles : cap, kSortThreads, sort_smem<RADIX>(), s>>>(
-                keys0, keys1, vals0, vals1, m, look0, look1, h);
-            return;
-        }
-    }
     // tiles arrive by bulk copies only when both buffers' rows are 16-byte aligned
     const bool aligned = ((reinterpret_cast<uintptr_t>(keys0) | reinterpret_cast<uintptr_t>(keys1) |
                            reinterpret_cast<uintptr_t>(vals0) | reinterpret_cast<uintptr_t>(vals1)) & 15u) == 0;
+    if constexpr (SLOT != kClassSlot) {
+        // the 9-bit top pass measured faster on persistent CTAs taking tile
+        // after tile (4.46 against 4.65 ms at 537M keys; the 8-bit passes
+        // slower: 3.87-4.08 against 3.62-3.71 ms)
+        if (persist || (RADIX == kMaxRadix && aligned)) {
+            const unsigned cap = unsigned(sm_count()) * PH0_SORT_MIN_BLOCKS;
+            if (aligned)
+                k_onesweep<RADIX, SLOT, true, true><<<tiles < cap ? tiles : cap, kSortThreads, sort_smem<RADIX>(), s>>>(
+                    keys0, keys1, vals0, vals1, m, look0, look1, h);
+            else
+                k_onesweep<RADIX, SLOT, false, true><<<tiles < cap ? tiles : cap, kSortThreads, sort_smem<RADIX>(), s>>>(
+                    keys0, keys1, vals0, vals1, m, look0, look1, h);
+            return;
+        }
+    }
     constexpr int TT = slot_threads<RADIX>();
     if (aligned)
         k_onesweep<RADIX, SLOT, true, false, TT><<<tiles, TT, sort_smem<RADIX, TT>(), s>>>(
