@@ -1,8 +1,8 @@
 """Seeded random clouds of every kind the parity cases cover (uniform,
 Gaussian mixtures, duplicates, exponent gaps, signed zeros, lattices, two
 crowded clusters, perturbed simplices, noisy circles) with random sizes and
-dimensions: the whole path and the early-terminating path against the
-oracle, bit for bit."""
+dimensions: the whole path, the early-terminating path and the large-cloud
+form against the oracle, bit for bit."""
 import numpy as np
 import pytest
 
@@ -65,3 +65,5 @@ def test_random_clouds_bit_exact(seed):
         pts = torch.from_numpy(x).cuda()
         assert _equal(ph0.barcodes(pts).numpy(), want), (seed, kind, x.shape)
         assert _equal(ph0.barcodes_early(pts, rounds=True).numpy(), want), (seed, kind, x.shape, "early")
+        # the large-cloud form (edge-index records), forced on
+        assert _equal(ph0.barcodes(pts, tuning={"wide_ids": 1}).numpy(), want), (seed, kind, x.shape, "wide")
