@@ -467,7 +467,9 @@ def run_h1(args, dev):
         out[f"uniform{n}_2d"] = {"ms": ms, "triangles": st["n_triangles"], "bars": st["n_bars"],
                                  "triangles_per_s": st["n_triangles"] / (ms * 1e-3), "rounds": st["rounds"],
                                  "max_column": st["max_column"], "pool_entries": st["pool_entries"],
-                                 "nonzero_bars": int((bars["death_sq"] > bars["birth_sq"]).sum())}
+                                 "nonzero_bars": int((bars["death_sq"] > bars["birth_sq"]).sum()),
+                                 "stage_ms": {k: round(st[k], 4) for k in
+                                              ("edges_ms", "triangles_ms", "reduce_ms", "emit_ms")}}
     if not args.no_cpu_baseline:
         import oracle
         x = inputs.uniform(256, 2, seed=20260109 + 256)
@@ -475,7 +477,8 @@ def run_h1(args, dev):
         oracle.h1(x)
         dt = time.perf_counter() - t0
         out["oracle_uniform256_2d"] = {"ms": 1e3 * dt, "cores": 1, "kind": "oracle"}
-    out["timing"] = "host clock around the synchronous call (workspace allocated inside)"
+    out["timing"] = ("host clock around the synchronous call (workspace allocated inside); "
+                     "stage_ms: CUDA events on the call's stream, last call")
     return out
 
 

@@ -318,6 +318,10 @@ typedef struct {
     int64_t pool_entries;       /* stored entries of reduced, non-apparent columns   */
     int32_t rounds;             /* ordering rounds over all windows                  */
     int32_t max_column;         /* longest column met under reduction                */
+    float edges_ms;             /* device time: steps 1-3 of dimension 0 (edge order) */
+    float triangles_ms;         /* ... the triangles written and sorted              */
+    float reduce_ms;            /* ... apparent pairs and the windows of rounds      */
+    float emit_ms;              /* ... the bars compacted and written                */
 } ph0_h1_stats;
 
 /* Workspace bytes of ph0_h1() for n points in dimension d (0 on invalid sizes;

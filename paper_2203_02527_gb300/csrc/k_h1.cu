@@ -462,7 +462,7 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
 // chunk prefixes; bars: n(n-1)/2 - (n-1) entries.  Asynchronous on s.
 cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, const uint64_t *ek1,
                    const uint32_t *ev0, const uint32_t *ev1, const Header *esort, const uint32_t *cpref,
-                   Header *h, ph0_h1bar *bars, cudaStream_t s) {
+                   Header *h, ph0_h1bar *bars, cudaStream_t s, cudaEvent_t after_sort, cudaEvent_t after_reduce) {
     const int64_t m = n_edges(n), T = H.T;
     Header *th = at<Header>(ws, H.thdr);
     H1Counters *c = at<H1Counters>(ws, H.cnt);
@@ -489,6 +489,7 @@ cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, 
     if (e == cudaSuccess)
         e = launch_sort_passes(tk0, tk1, tv0, tv1, T, at<uint64_t>(ws, H.tlook[0]), at<uint64_t>(ws, H.tlook[1]), th,
                                s, false);
+    if (e == cudaSuccess && after_sort) e = cudaEventRecord(after_sort, s);
     if (e != cudaSuccess) return e;
     // 3. apparent pairs; 4. the other columns, window by window
     k_h1_apparent<<<grid, 256, 0, s>>>(tk0, tk1, th, T, own_tri, pair_low);
@@ -528,6 +529,7 @@ cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, 
         e = cudaLaunchCooperativeKernel((const void *)k_h1_window, dim3(wgrid), dim3(kH1Threads), params, 0, s);
         if (e != cudaSuccess) return e;
     }
+    if (after_reduce && (e = cudaEventRecord(after_reduce, s)) != cudaSuccess) return e;
     // 5. the bars in triangle order
     uint32_t *ccount = at<uint32_t>(ws, H.ccount);
     k_h1_count<<<unsigned(H.chunks), 256, 0, s>>>(pair_low, T, ccount);

@@ -59,7 +59,7 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s);
 cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s);
 cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, const uint64_t *ek1,
                    const uint32_t *ev0, const uint32_t *ev1, const Header *esort, const uint32_t *cpref,
-                   Header *h, ph0_h1bar *bars, cudaStream_t s);
+                   Header *h, ph0_h1bar *bars, cudaStream_t s, cudaEvent_t after_sort, cudaEvent_t after_reduce);
 cudaError_t h1_counters(const void *ws, const H1Layout &H, uint64_t out[5]);
 cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
@@ -673,13 +673,30 @@ int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *ba
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
+    // stage events: start | edges | triangles sorted | reduced | end
+    cudaEvent_t ev[5] = {};
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 5 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < made - 1; ++i) cudaEventDestroy(ev[i]);
+        return PH0_ECUDA;
+    }
     // steps 1-3 of dimension 0: the edge order and the de-duplication
-    cudaError_t e = begin_call(ws, L, s, t.top_bits);
+    e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
-    if (e == cudaSuccess && nbars > 0) e = run_h1(ws, H, n, k0, k1, v0, v1, h, cpref, h, bars_dev, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess && nbars > 0) e = run_h1(ws, H, n, k0, k1, v0, v1, h, cpref, h, bars_dev, s, ev[2], ev[3]);
+    if (e == cudaSuccess && nbars <= 0) e = cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess && nbars <= 0) e = cudaEventRecord(ev[3], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
     uint64_t cnt[5] = {0, 0, 0, 0, 0};
     int32_t status = PH0_OK;
     if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);
@@ -693,6 +710,10 @@ int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *ba
         stats->pool_entries = int64_t(cnt[1]);
         stats->rounds = int32_t(cnt[2]);
         stats->max_column = int32_t(cnt[3]);
+        stats->edges_ms = ms[0];
+        stats->triangles_ms = ms[1];
+        stats->reduce_ms = ms[2];
+        stats->emit_ms = ms[3];
     }
     return status;
 }
