@@ -139,12 +139,19 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
 // Shared memory of one pass: the tile's keys (input, then in sorted order),
 // its values (input, and in sorted order), per-warp digit counts, per-digit
 // destination offsets.
+// The 8-bit passes reorder the values in place (12 bytes of shared memory
+// per key instead of 16), which lets four CTAs share an SM (3.51-3.69 ms per
+// pass at 537M keys against 3.63-3.98 ms with three); the 9-bit pass keeps a
+// separate array for the sorted values and three CTAs per SM (its larger
+// counters do not leave room for a fourth: 5.20 against 4.44 ms).
+template <int RADIX>
+__host__ __device__ constexpr bool sort_inplace() { return RADIX == kRadix; }
 template <int RADIX, int THREADS = kSortThreads>
 struct SortSmem {
     static constexpr int W = THREADS / 32;
     uint64_t keys[kSortTile];          // input keys, then the tile's keys in sorted order
-    uint32_t vals_in[kSortTile];       // input values; after the scatter, the top-digit histogram
-    uint32_t vals[kSortTile];          // values in sorted order
+    uint32_t vals_in[kSortTile];       // input values (in place: then in sorted order)
+    uint32_t vals[sort_inplace<RADIX>() ? 4 : kSortTile];  // values in sorted order (not in place)
     uint16_t whist[W][RADIX];          // counts, then the local position of each warp's first item
     uint32_t gofs[RADIX];              // global position of sorted tile index 0 of each digit's run (mod 2^32)
     uint32_t scan[W + 1];
@@ -152,6 +159,7 @@ struct SortSmem {
     unsigned long long mbar;           // completion of the tile's bulk copies
 };
 static_assert(kMaxRadix <= kSortTile, "top-digit histogram lives in vals_in");
+static_assert(2 * kRadix * 4 <= 8 * kRadix * 2, "in place: the next passes' histogram lives in whist");
 
 // ---- bulk (TMA) copies global -> shared with an mbarrier -------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -280,9 +288,6 @@ __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t
     return excl;
 }
 
-#ifndef PH0_SORT_MIN_BLOCKS
-#define PH0_SORT_MIN_BLOCKS 3
-#endif
 
 // One radix pass (pass index = SLOT).  Pass p reads buffer p&1 and writes
 // buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
@@ -290,17 +295,18 @@ __device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t
 // look[(p+1)&1] for the next pass (whose previous user, pass p-1, is done).
 // THREADS: 256 (kSortItems keys each), or 512 with half as many keys each
 // (the same tile): one digit per thread in a 9-bit pass.
-template <int THREADS>
-constexpr int sort_min_blocks() { return THREADS == kSortThreads ? PH0_SORT_MIN_BLOCKS : 2; }
+template <int RADIX, int THREADS = kSortThreads>
+__host__ __device__ constexpr int sort_min_blocks() { return THREADS == kSortThreads ? (sort_inplace<RADIX>() ? 4 : 3) : 2; }
 
 template <int RADIX, int SLOT, bool ALIGNED, bool PERSIST = false, int THREADS = kSortThreads>
-__global__ void __launch_bounds__(THREADS, sort_min_blocks<THREADS>())
+__global__ void __launch_bounds__(THREADS, (sort_min_blocks<RADIX, THREADS>()))
 k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
            uint64_t *look0, uint64_t *look1, Header *h) {
     constexpr int T = THREADS, IT = kSortTile / THREADS, TILE = kSortTile, W = T / 32;
     static_assert(IT * T == TILE, "every instance sorts the same tiles");
 
     constexpr int DPT = RADIX / T;  // digits per thread
+    constexpr bool INPL = sort_inplace<RADIX>();
     static_assert(RADIX % T == 0 && RADIX <= kMaxRadix, "radix");
     static_assert((TILE & (TILE - 1)) == 0, "tile positions are masked to the tile");
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -510,14 +516,38 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         __syncthreads();
 
         // ---- reorder keys and values by digit in shared memory ----
+        if constexpr (INPL) {
+            // keys from registers into their array; then every value into a
+            // register before any is written back into its own array
 #pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            const uint32_t dj = dr[j] >> 16;
-            const int loc = wloc + j * 32 + lane;
-            if (dj < RADIX) {
-                const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
-                S.keys[pos] = k[j];
-                S.vals[pos] = full ? S.vals_in[loc] : vin[base + loc];
+            for (int j = 0; j < IT; ++j) {
+                const uint32_t dj = dr[j] >> 16;
+                if (dj < RADIX) {
+                    const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);
+                    S.keys[pos] = k[j];
+                    dr[j] = (dj << 16) | pos;
+                }
+            }
+            uint32_t vj[IT];
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const int loc = wloc + j * 32 + lane;
+                vj[j] = full ? S.vals_in[loc] : (loc < valid ? vin[base + loc] : 0u);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < IT; ++j)
+                if ((dr[j] >> 16) < RADIX) S.vals_in[dr[j] & 0xffffu] = vj[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const uint32_t dj = dr[j] >> 16;
+                const int loc = wloc + j * 32 + lane;
+                if (dj < RADIX) {
+                    const uint32_t pos = (S.whist[warp][dj] + (dr[j] & 0xffffu)) & (TILE - 1);  // in range by construction
+                    S.keys[pos] = k[j];
+                    S.vals[pos] = full ? S.vals_in[loc] : vin[base + loc];
+                }
             }
         }
 
@@ -532,7 +562,8 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             }
             S.gofs[d] = excl - lstart[q];  // wraps below 0; positions are < 2^32
         }
-        uint32_t *s_next = S.vals_in;  // dead once every thread has finished the scatter
+        // dead once every thread has finished the scatter (in place: whist, dead after the reorder)
+        uint32_t *s_next = INPL ? reinterpret_cast<uint32_t *>(&S.whist[0][0]) : S.vals_in;
         if (hist_top) {
             __syncthreads();
             for (int i = tid; i < kMaxRadix; i += T) s_next[i] = 0;
@@ -547,7 +578,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan, cd)] + uint32_t(i);
             if (g >= m32) continue;  // never taken when the counts are consistent
             kout[g] = key;
-            vout[g] = S.vals[i];
+            vout[g] = INPL ? S.vals_in[i] : S.vals[i];
             if (hist_top) {  // the two top passes' digits: low and high byte of t
                 const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
                 atomicAdd(&s_next[t & (kRadix - 1)], 1u);
@@ -859,7 +890,7 @@ cudaError_t prepare_sort_kernels() {
     return e;
 }
 
-// persist: run the persistent instance on PH0_SORT_MIN_BLOCKS CTAs per SM,
+// persist: run the persistent instance on sort_min_blocks<RADIX>() CTAs per SM,
 // for passes that usually return at once (a grid of one CTA per tile costs
 // ~0.1 ms at 131k tiles even then).
 template <int RADIX, int SLOT>
@@ -873,7 +904,7 @@ static void launch_slot(unsigned tiles, uint64_t *keys0, uint64_t *keys1, uint32
         // after tile (4.46 against 4.65 ms at 537M keys; the 8-bit passes
         // slower: 3.87-4.08 against 3.62-3.71 ms)
         if (persist || (RADIX == kMaxRadix && aligned)) {
-            const unsigned cap = unsigned(sm_count()) * PH0_SORT_MIN_BLOCKS;
+            const unsigned cap = unsigned(sm_count()) * sort_min_blocks<RADIX>();
             if (aligned)
                 k_onesweep<RADIX, SLOT, true, true><<<tiles < cap ? tiles : cap, kSortThreads, sort_smem<RADIX>(), s>>>(
                     keys0, keys1, vals0, vals1, m, look0, look1, h);
