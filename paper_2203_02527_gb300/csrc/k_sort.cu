@@ -136,6 +136,29 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
         if (s_top[i]) atomicAdd(&h->hist_top_mod[i], s_top[i]);
 }
 
+// The values of the top part that occur, numbered in increasing order (a
+// single top pass only): when at most kRadix occur, the top pass runs on the
+// 8-bit instance of slot 6 with digit top_lut[t] (t the top part less that of
+// kmin), which orders the keys as t does; the digits' histogram is written to
+// hist[kLowPasses].  On the benchmark cloud 211 of the 266 values in the
+// top part's span occur.
+__global__ void __launch_bounds__(kMaxRadix) k_top_compact(Header *h) {
+    __shared__ uint32_t s_warp[kMaxRadix / 32 + 1];
+    const int t = threadIdx.x;
+    const Plan plan = make_plan(h);
+    uint32_t c = 0;
+    if (plan.top == 1) c = h->hist_top_mod[(uint32_t(t) + uint32_t(plan.kmin >> kTopShift)) & (kMaxRadix - 1)];
+    uint32_t tot;
+    const uint32_t idx = block_excl_scan<kMaxRadix>(c != 0 ? 1u : 0u, s_warp, tot);
+    const bool compact = plan.top == 1 && tot <= uint32_t(kRadix);
+    if (compact) {
+        h->top_lut[t] = uint8_t(c != 0 ? idx : 0u);  // t that occur nowhere are never looked up
+        if (c != 0) h->hist[kLowPasses][idx] = c;
+        if (t < kRadix && uint32_t(t) >= tot) h->hist[kLowPasses][t] = 0;
+    }
+    if (t == 0) h->top_compact = compact ? 1 : 0;
+}
+
 // Shared memory of one pass: the tile's keys (input, then in sorted order),
 // its values (input, and in sorted order), per-warp digit counts, per-digit
 // destination offsets.
@@ -207,15 +230,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
 
 // Digit of a key in pass slot SLOT: slots 0..5 are the raw bytes of bits
 // 0..47; slot 6 is the top part (all of it if it has at most 9 bits, else its
-// low byte); slot 7 is the high byte of a 16-bit top part.
+// low byte), or, in the 8-bit instance of slot 6, the number of the top
+// part among the values that occur (k_top_compact); slot 7 is the high byte
+// of a 16-bit top part.
 // Slot kClassSlot (the early path's partition): the class of the key's bin,
 // the number of class bounds bound[1..nc-1] at or below the bin.
 struct ClassDigit {
     uint64_t kmin;
     int shift, nc;
     const uint32_t *bound;  // shared memory
+    const uint8_t *lut;     // shared memory: top_lut (the 8-bit instance of slot 6)
 };
-template <int SLOT>
+template <int SLOT, int RADIX>
 __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p, const ClassDigit &cd) {
     if constexpr (SLOT == kClassSlot) {
         const uint32_t bin = uint32_t((key - cd.kmin) >> cd.shift);
@@ -226,6 +252,7 @@ __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p, cons
     } else {
         if (SLOT < kLowPasses) return uint32_t(key >> (kRadixBits * SLOT)) & (kRadix - 1);
         const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+        if (SLOT == kLowPasses && RADIX == kRadix) return cd.lut[t & (kMaxRadix - 1)];
         if (SLOT == kLowPasses) return p.top == 1 ? t : (t & (kRadix - 1));
         return t >> kRadixBits;
     }
@@ -314,6 +341,12 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 
     const Plan plan = make_plan(h);
     if (SLOT != kClassSlot && SLOT >= plan.passes) return;
+    // slot 6 has two instances, launched one after the other: the 8-bit one
+    // works when k_top_compact found at most kRadix top values, the other else
+    constexpr bool COMPACT = SLOT == kLowPasses && RADIX == kRadix;
+    if constexpr (SLOT == kLowPasses) {
+        if (COMPACT != (ld_volatile(&h->top_compact) != 0)) return;
+    }
     const uint64_t *kin = (SLOT & 1) ? keys1 : keys0;
     uint64_t *kout = (SLOT & 1) ? keys0 : keys1;
     const uint32_t *vin = (SLOT & 1) ? vals1 : vals0;
@@ -329,10 +362,15 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         mbar_init(&S.mbar, 1);
     }
     ClassDigit cd{};
+    if constexpr (COMPACT) {
+        __shared__ uint8_t s_lut[kMaxRadix];
+        for (int i = tid; i < kMaxRadix; i += T) s_lut[i] = h->top_lut[i];
+        cd.lut = s_lut;
+    }
     if constexpr (SLOT == kClassSlot) {
         __shared__ uint32_t s_bound[kPrefixClasses + 1];
         if (tid <= kPrefixClasses) s_bound[tid] = h->part_bound[tid];
-        cd = ClassDigit{h->part_kmin, h->part_shift, h->part_nc, s_bound};
+        cd = ClassDigit{h->part_kmin, h->part_shift, h->part_nc, s_bound, nullptr};
     }
     __syncthreads();
     // PERSIST: the instance launched on fewer CTAs than tiles (passes that
@@ -388,7 +426,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
                 // a single top pass: its digit t = (key >> kTopShift) - (kmin >> kTopShift)
                 // is below kMaxRadix, so its count is hist_top_mod[r] with
                 // r = (t + (kmin >> kTopShift)) mod kMaxRadix (no other digit maps to r)
-                bucket[q] = (SLOT == kLowPasses && plan.top == 1)
+                bucket[q] = (SLOT == kLowPasses && !COMPACT && plan.top == 1)
                                 ? h->hist_top_mod[(uint32_t(tid * DPT + q) + uint32_t(plan.kmin >> kTopShift)) &
                                                   (kMaxRadix - 1)]
                                 : h->hist[SLOT == kClassSlot ? 0 : SLOT][tid * DPT + q];
@@ -427,7 +465,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
         const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
         for (int j = 0; j < IT; ++j) {
-            const uint32_t dj = (full || wloc + j * 32 + lane < valid) ? slot_digit<SLOT>(k[j], plan, cd)
+            const uint32_t dj = (full || wloc + j * 32 + lane < valid) ? slot_digit<SLOT, RADIX>(k[j], plan, cd)
                                                                        : uint32_t(RADIX);
             // lanes with the same digit.  8-bit digits (raw mantissa bytes, about
             // uniform: a warp holds ~30 distinct values): intersect one ballot per
@@ -575,7 +613,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 #pragma unroll 4
         for (int i = tid; i < valid; i += T) {
             const uint64_t key = S.keys[i];
-            const uint32_t g = S.gofs[slot_digit<SLOT>(key, plan, cd)] + uint32_t(i);
+            const uint32_t g = S.gofs[slot_digit<SLOT, RADIX>(key, plan, cd)] + uint32_t(i);
             if (g >= m32) continue;  // never taken when the counts are consistent
             kout[g] = key;
             vout[g] = INPL ? S.vals_in[i] : S.vals[i];
@@ -884,6 +922,7 @@ cudaError_t prepare_sort_kernels() {
     if (e == cudaSuccess) e = set_attr<kRadix, 3>();
     if (e == cudaSuccess) e = set_attr<kRadix, 4>();
     if (e == cudaSuccess) e = set_attr<kRadix, 5>();
+    if (e == cudaSuccess) e = set_attr<kRadix, 6>();
     if (e == cudaSuccess) e = set_attr<kMaxRadix, 6>();
     if (e == cudaSuccess) e = set_attr<kRadix, 7>();
     if (e == cudaSuccess) e = set_attr<kRadix, kClassSlot>();
@@ -936,7 +975,11 @@ cudaError_t launch_sort_pass(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, 
         case 3: PH0_SLOT(kRadix, 3); break;
         case 4: PH0_SLOT(kRadix, 4); break;
         case 5: PH0_SLOT(kRadix, 5); break;
-        case 6: PH0_SLOT(kMaxRadix, 6); break;
+        case 6:  // two instances, one of which returns at once (k_top_compact)
+            k_top_compact<<<1, kMaxRadix, 0, s>>>(h);
+            PH0_SLOT(kRadix, 6);
+            PH0_SLOT(kMaxRadix, 6);
+            break;
         case 7: PH0_SLOT(kRadix, 7); break;
         default: PH0_SLOT(kRadix, kClassSlot); break;
     }

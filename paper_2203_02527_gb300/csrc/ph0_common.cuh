@@ -109,6 +109,11 @@ struct Header {
     // when the top part spans less than kMaxRadix values (a single top
     // pass), it is the top digit's histogram rotated by kmin >> kTopShift
     uint32_t hist_top_mod[kMaxRadix];
+    // the single top pass on 8-bit digits (k_top_compact): set when at most
+    // kRadix values of the top part occur; top_lut numbers them in order
+    int32_t top_compact;
+    uint32_t pad3;
+    uint8_t top_lut[kMaxRadix];
 };
 
 constexpr size_t kHeaderBytes = 32768;
