@@ -446,14 +446,15 @@ def run_descent(args, dev):
 
 def run_h1(args, dev):
     """First homology (ph0_h1) on uniform points in the unit square, the
-    paper's workload (at 256 points and at its largest N, 700): host clock around the
-    synchronous call; the oracle's literal reduction timed beside it on one
+    paper's workload (256 points, its largest N of 700, and the largest cloud
+    ph0_h1 takes, 4096): host clock around the synchronous call, stage times
+    from CUDA events; the oracle's literal reduction timed beside it on one
     core where it finishes in seconds."""
     import torch
 
     from paper_2203_02527_gb300 import ph0
     out = {}
-    for n in (256, 700):
+    for n in (256, 700, 4096):
         x = inputs.uniform(n, 2, seed=20260109 + n)
         pts = torch.from_numpy(x).to(dev)
         times = []
@@ -465,11 +466,12 @@ def run_h1(args, dev):
                 times.append(time.perf_counter() - t0)
         ms = 1e3 * float(np.mean(times))
         out[f"uniform{n}_2d"] = {"ms": ms, "triangles": st["n_triangles"], "bars": st["n_bars"],
-                                 "triangles_per_s": st["n_triangles"] / (ms * 1e-3), "rounds": st["rounds"],
+                                 "triangles_per_s": st["n_triangles"] / (ms * 1e-3), "apparent": st["apparent"],
+                                 "reduced_columns": st["reduced"], "additions": st["additions"],
                                  "max_column": st["max_column"], "pool_entries": st["pool_entries"],
                                  "nonzero_bars": int((bars["death_sq"] > bars["birth_sq"]).sum()),
                                  "stage_ms": {k: round(st[k], 4) for k in
-                                              ("edges_ms", "triangles_ms", "reduce_ms", "emit_ms")}}
+                                              ("edges_ms", "scan_ms", "reduce_ms", "emit_ms")}}
     if not args.no_cpu_baseline:
         import oracle
         x = inputs.uniform(256, 2, seed=20260109 + 256)

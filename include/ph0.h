@@ -314,25 +314,32 @@ typedef struct {
 
 typedef struct {
     int64_t n_bars;             /* bars written: n(n-1)/2 - (n-1)                    */
-    int64_t n_triangles;        /* n(n-1)(n-2)/6                                     */
-    int64_t pool_entries;       /* stored entries of reduced, non-apparent columns   */
-    int32_t rounds;             /* ordering rounds over all windows                  */
-    int32_t max_column;         /* longest column met under reduction                */
+    int64_t n_triangles;        /* n(n-1)(n-2)/6, from the per-edge triangle counts  */
+    int64_t apparent;           /* bars of apparent pairs (no column addition)       */
+    int64_t reduced;            /* columns reduced by additions (positive edges that
+                                   are the diameter of no triangle)                 */
+    int64_t additions;          /* column additions over all reduced columns         */
+    int64_t max_column;         /* longest column met under reduction                */
+    int64_t pool_entries;       /* triangle keys held by the reduced columns         */
     float edges_ms;             /* device time: steps 1-3 of dimension 0 (edge order) */
-    float triangles_ms;         /* ... the triangles written and sorted              */
-    float reduce_ms;            /* ... apparent pairs and the windows of rounds      */
-    float emit_ms;              /* ... the bars compacted and written                */
+    float scan_ms;              /* ... positions, the triangles of each diameter     */
+    float reduce_ms;            /* ... spanning forest and the reduced columns       */
+    float emit_ms;              /* ... ranks in triangle order and the bars          */
 } ph0_h1_stats;
 
 /* Workspace bytes of ph0_h1() for n points in dimension d (0 on invalid sizes;
- * 3 <= n needs triangles, n <= 1024). */
+ * 3 <= n needs triangles, n <= 4096). */
 size_t ph0_h1_workspace_bytes(int64_t n, int32_t d);
 
 /* First-homology bars of the cloud (steps 1-3 of the dimension-0 path for the
- * edge order and a, then the triangles).  bars_dev: ph0_h1bar[n(n-1)/2 - (n-1)]
- * (none for n <= 2).  1 <= n <= 1024.  Synchronous: waits for `stream` and
- * returns the device status; PH0_ETOOBIG also when a column under reduction
- * would exceed 512 entries.  stats may be NULL. */
+ * edge order and a, then the pairs).  The pairs are computed through the
+ * coboundary matrix, whose reduction has the same pairs: apparent pairs for
+ * every edge that is the diameter of some triangle, the dimension-0 spanning
+ * forest's columns cleared, the other columns reduced from the latest edge
+ * down.  bars_dev: ph0_h1bar[n(n-1)/2 - (n-1)] (none for n <= 2), in triangle
+ * order.  1 <= n <= 4096.  Synchronous: waits for `stream` and returns the
+ * device status; PH0_ETOOBIG also when a column under reduction or the kept
+ * reduced columns outgrow the workspace's room for them.  stats may be NULL. */
 int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *bars_dev, void *ws,
            size_t ws_bytes, void *stream, ph0_h1_stats *stats);
 

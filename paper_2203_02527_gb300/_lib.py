@@ -102,9 +102,10 @@ H1_BAR_BYTES = H1_DTYPE.itemsize  # 72
 
 class H1Stats(ctypes.Structure):
     _fields_ = [("n_bars", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
-                ("pool_entries", ctypes.c_int64), ("rounds", ctypes.c_int32),
-                ("max_column", ctypes.c_int32), ("edges_ms", ctypes.c_float),
-                ("triangles_ms", ctypes.c_float), ("reduce_ms", ctypes.c_float),
+                ("apparent", ctypes.c_int64), ("reduced", ctypes.c_int64),
+                ("additions", ctypes.c_int64), ("max_column", ctypes.c_int64),
+                ("pool_entries", ctypes.c_int64), ("edges_ms", ctypes.c_float),
+                ("scan_ms", ctypes.c_float), ("reduce_ms", ctypes.c_float),
                 ("emit_ms", ctypes.c_float)]
 
     def as_dict(self):

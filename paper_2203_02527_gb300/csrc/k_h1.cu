@@ -2,90 +2,90 @@
 // the paper names (Rawson, Sec. 1 and Sec. 4.2: higher-order homology).  The
 // 2-skeleton adds a triangle on three points once its three edges are
 // present (Sec. 1, the recursive rule): at its diameter, the latest of its
-// edges in the sorted edge order of step 2.  The boundary matrix has a row
-// per edge and a column per triangle (its three edges, entries t^a over
-// F2[t], which reduce like their F2 supports, as in dimension 0); reducing
-// the columns left to right, each nonzero reduced column pairs its low edge
-// (a positive edge, one that closed a cycle) with its triangle: the bar
+// edges in the sorted edge order of step 2.  Its boundary matrix has a row
+// per edge and a column per triangle (entries t^a over F2[t], which reduce
+// like their F2 supports, as in dimension 0), the triangles in the order
+// (diameter position, u, v, w).  Reducing it left to right pairs each
+// positive edge (one that closed a cycle) with a triangle: the bar
 // (a(edge), a(diameter)).  The full simplex has no first homology, so every
 // positive edge is paired: n(n-1)/2 - (n-1) bars.
 //
-// On the GPU:
-//   1. the dimension-0 path's sort and de-duplication give every edge its
-//      position p in the edge order and its index a(p) (a_of);
-//   2. every triangle is written as (diameter position, (u << 20) | (v << 10)
-//      | w) in lexicographic order and sorted stably by diameter with the
-//      radix sort of step 2: the triangle order (diameter, u, v, w);
-//   3. apparent pairs: the first triangle of each diameter owns that edge
-//      with its unreduced column (no earlier column can reach a low that
-//      late: an earlier triangle's diameter, hence its low, is smaller);
-//   4. the other triangles, in windows of consecutive positions, by a
-//      persistent cooperative kernel in rounds: each column is added the
-//      columns of final owners of its low until it is zero or its low has no
-//      final owner (in parallel, one thread per column); then, in position
-//      order, a column becomes the final owner of its low L when every
-//      earlier column still under reduction has a low below L (lows only
-//      fall, so none of them can reach L).  The lowest such column always
-//      qualifies, so every round finalizes at least one column, and every
-//      column is added only columns to its left: the pairs are those of the
-//      left-to-right reduction;
-//   5. the paired triangles are compacted in triangle order into the bars.
-// Columns under reduction live in fixed slots of kH1Cap entries; the final
-// columns of non-apparent owners in a pool.  A column that outgrows its slot,
-// or a full pool, stops the kernel with PH0_ETOOBIG (uniform points in the
-// plane: columns up to 384 entries at n = 1024, within the 512 of a slot).
+// The GPU computes the same pairs through the coboundary matrix (the
+// transpose with both orders reversed), whose left-to-right reduction has
+// the same pairs (persistence pairs of homology and cohomology coincide):
+// a column per edge, taken from the latest edge to the earliest, whose pivot
+// is its earliest triangle.  Three facts make it short:
+//   * clearing: the n-1 edges that end a class in dimension 0 are pivots of
+//     the dimension-0 coboundary, so their columns are dropped;
+//   * apparent pairs: when edge e is the diameter of some triangle, the
+//     first such triangle t (in triangle order) is e's earliest coface and e
+//     is t's latest face; no column processed before e (a later edge) can
+//     contain t, so (e, t) is a pair with no column addition.  The first such
+//     triangle is the one whose third vertex w is smallest (the order of
+//     sorted (a, b, w) follows w);
+//   * an edge that is the diameter of no triangle is either a spanning-forest
+//     edge (a minimum spanning forest lies within these edges, by the cycle
+//     property) or a positive edge whose column must be reduced; these are
+//     few (63 at 256 uniform points in the plane, 177 at 700).
+// Steps:
+//   1. the dimension-0 sort and de-duplication give every edge its position
+//      p and its index a(p); a matrix P[a][w] of positions;
+//   2. one warp per edge: the triangles of which it is the diameter (count
+//      and smallest third vertex), i.e. the apparent pairs and, by a prefix
+//      sum of the counts, the rank of every triangle in triangle order;
+//   3. the edges that are the diameter of no triangle, in order: Kruskal
+//      (one thread) marks the spanning-forest edges; the rest are listed;
+//   4. one CTA reduces the listed columns from the latest edge down: a
+//      column is the sorted list of its triangle keys; while its pivot has
+//      an owner (the apparent pair of the pivot's diameter edge, or an
+//      earlier reduced column), the owner's column is added (sorted
+//      symmetric difference); the pivot left is claimed;
+//   5. the bars, in triangle order, from the prefix sums of the counts.
 #include "ph0_common.cuh"
 
 namespace ph0 {
 
-constexpr int kH1Threads = 512;
+constexpr uint32_t kH1NoPos = 0xffffffffu;
+constexpr int kH1VB = kH1VertexBits;
+constexpr uint64_t kH1VMask = (uint64_t(1) << kH1VB) - 1;
 
-__host__ __device__ __forceinline__ uint32_t h1_pack(uint32_t u, uint32_t v, uint32_t w) {
-    return (u << 20) | (v << 10) | w;
+// Key of the triangle {a, b, w} (distinct vertices) with diameter position dpos.
+__device__ __forceinline__ uint64_t h1_key(uint64_t dpos, uint32_t a, uint32_t b, uint32_t w) {
+    uint32_t x = a, y = b, z = w;
+    if (x > y) { const uint32_t t = x; x = y; y = t; }
+    if (y > z) { const uint32_t t = y; y = z; z = t; }
+    if (x > y) { const uint32_t t = x; x = y; y = t; }
+    return (dpos << (3 * kH1VB)) | (uint64_t(x) << (2 * kH1VB)) | (uint64_t(y) << kH1VB) | uint64_t(z);
 }
-__device__ __forceinline__ void h1_unpack(uint32_t t, uint32_t &u, uint32_t &v, uint32_t &w) {
-    u = t >> 20;
-    v = (t >> 10) & 1023u;
-    w = t & 1023u;
+__device__ __forceinline__ void h1_key_uvw(uint64_t k, uint32_t &u, uint32_t &v, uint32_t &w) {
+    u = uint32_t((k >> (2 * kH1VB)) & kH1VMask);
+    v = uint32_t((k >> kH1VB) & kH1VMask);
+    w = uint32_t(k & kH1VMask);
+}
+__device__ __forceinline__ uint32_t h1_key_dpos(uint64_t k) { return uint32_t(k >> (3 * kH1VB)); }
+
+// Endpoints a < b of the sorted edge at p; false for a record that is not an
+// edge of the cloud (never, with consistent records).
+__device__ __forceinline__ bool h1_uv(const uint32_t *vals, int64_t p, int64_t n, uint32_t &a, uint32_t &b) {
+    record_uv(vals[p], false, n, a, b);
+    return a < b && int64_t(b) < n;
 }
 
-// Sorted positions of the three edges of triangle (u, v, w).
-__device__ __forceinline__ void h1_tri_edges(const uint32_t *posof, int64_t n, uint32_t u, uint32_t v,
-                                             uint32_t w, uint32_t (&e)[3]) {
-    uint32_t a = posof[edge_index(n, u, v)], b = posof[edge_index(n, u, w)], c = posof[edge_index(n, v, w)];
-    if (a > b) { const uint32_t t = a; a = b; b = t; }
-    if (b > c) { const uint32_t t = b; b = c; c = t; }
-    if (a > b) { const uint32_t t = a; a = b; b = t; }
-    e[0] = a;
-    e[1] = b;
-    e[2] = c;
-}
+// Column additions of one call before it stops with PH0_ETOOBIG (776 at 700
+// uniform points in the plane).
+constexpr unsigned long long kH1MaxAdditions = 1ull << 22;
 
-// out = x (+) y over F2: the symmetric difference of two ascending lists;
-// returns its length, or -1 if it would exceed cap.
-// (y_l2: y was written by another CTA, read it through L2)
-__device__ __forceinline__ int h1_symdiff(const uint32_t *x, int nx, const uint32_t *y, int ny, uint32_t *out,
-                                          int cap, bool y_l2) {
-    int i = 0, j = 0, k = 0;
-    uint32_t xi = nx > 0 ? x[0] : 0, yj = ny > 0 ? (y_l2 ? __ldcg(y) : y[0]) : 0;
-    while (i < nx || j < ny) {
-        uint32_t val;
-        if (j >= ny || (i < nx && xi < yj)) {
-            val = xi;
-            if (++i < nx) xi = x[i];
-        } else if (i >= nx || yj < xi) {
-            val = yj;
-            if (++j < ny) yj = y_l2 ? __ldcg(y + j) : y[j];
-        } else {  // equal rows: 1 + 1 = 0
-            if (++i < nx) xi = x[i];
-            if (++j < ny) yj = y_l2 ? __ldcg(y + j) : y[j];
-            continue;
-        }
-        if (k >= cap) return -1;
-        out[k++] = val;
-    }
-    return k;
-}
+// Counters of the last run (device; read back by h1_counters).
+struct H1Counters {
+    unsigned long long bars;        // bars written
+    unsigned long long zero;        // edges that are the diameter of no triangle
+    unsigned long long reduced;     // of them positive: columns reduced
+    unsigned long long forest;      // of them spanning-forest edges
+    unsigned long long additions;   // column additions
+    unsigned long long max_len;     // longest column met
+    unsigned long long pool_used;   // keys held by the reduced columns
+    unsigned long long nodes;       // pivots claimed by reduced columns
+};
 
 // -------------------------------------------------------------- step 1 ---
 // a_of[p]: 1-based index in D of the sorted edge at p, from the chunk
@@ -132,427 +132,582 @@ __global__ void k_h1_posof(const uint32_t *vals0, const uint32_t *vals1, const H
     }
 }
 
+// P[a][w]: position of edge {a, w}; kH1NoPos on the diagonal (so that w = a
+// never counts as an earlier edge).
+__global__ void k_h1_pmat(const uint32_t *posof, int64_t n, uint32_t *P) {
+    const int64_t nn = n * n;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nn; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t a = i / n, w = i - a * n;
+        P[i] = a == w ? kH1NoPos : posof[a < w ? edge_index(n, a, w) : edge_index(n, w, a)];
+    }
+}
+
 // -------------------------------------------------------------- step 2 ---
-// Triangles in lexicographic order: one warp per edge (u, v), its lanes over
-// the third vertices w > v; key = position of the triangle's diameter edge.
-__global__ void k_h1_tris(const uint32_t *posof, int64_t n, int64_t m, uint64_t *tkey, uint32_t *tval) {
+// One warp per edge position p = {a, b}: the third vertices w with both
+// {a, w} and {b, w} before p are the triangles of diameter p.  tcount[p]:
+// their number; tfirst[p]: the smallest w (-1 if none); scan_in[p]: 1 if
+// none (for the list of step 3).
+__global__ void k_h1_edges(const uint32_t *vals0, const uint32_t *vals1, const Header *esort, int64_t m,
+                           int64_t n, const uint32_t *P, uint32_t *tcount, int32_t *tfirst, uint64_t *scan_in) {
+    const uint32_t *vals = (make_plan(esort).passes & 1) ? vals1 : vals0;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const int64_t tot = n * (n - 1) * (n - 2) / 6;
-    for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        uint32_t u, v;
-        record_uv(uint32_t(e), true, n, u, v);  // the lexicographic edge index
-        // triangles (i, j, k) before (u, v, v+1): those with i < u, then
-        // those with i = u and u < j < v
-        const int64_t nu = n - u, nv = n - v;
-        const int64_t t0 = (tot - nu * (nu - 1) * (nu - 2) / 6) + ((nu - 1) * (nu - 2) / 2 - nv * (nv - 1) / 2);
-        const uint32_t puv = posof[e];
-        for (int64_t w = int64_t(v) + 1 + lane; w < n; w += 32) {
-            const uint32_t puw = posof[edge_index(n, u, w)], pvw = posof[edge_index(n, v, w)];
-            uint32_t d = puv > puw ? puv : puw;
-            d = d > pvw ? d : pvw;
-            const int64_t t = t0 + (w - v - 1);
-            tkey[t] = d;
-            tval[t] = h1_pack(u, v, uint32_t(w));
+    for (int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < m; p += warps) {
+        uint32_t a, b;
+        if (!h1_uv(vals, p, n, a, b)) {  // left out: the bar count then shows it
+            if (lane == 0) {
+                tcount[p] = 0;
+                tfirst[p] = -2;
+                scan_in[p] = 0;
+            }
+            continue;
+        }
+        const uint32_t *Pa = P + int64_t(a) * n, *Pb = P + int64_t(b) * n;
+        const uint32_t pp = uint32_t(p);
+        uint32_t cnt = 0;
+        int32_t first = -1;
+        for (int64_t w0 = 0; w0 < n; w0 += 32) {
+            const int64_t w = w0 + lane;
+            const bool ok = w < n && __ldg(Pa + w) < pp && __ldg(Pb + w) < pp;
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (first < 0 && bal) first = int32_t(w0) + __ffs(bal) - 1;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) {
+            tcount[p] = cnt;
+            tfirst[p] = first;
+            scan_in[p] = cnt == 0 ? 1u : 0u;
         }
     }
+}
+
+// ------------------------------------------------- exclusive prefix sums ---
+// out[i] = in[0] + ... + in[i-1] for i <= len (out[len] = the total), over
+// blocks of kH1ScanItems: per-block sums, their scan, then the blocks.
+__device__ __forceinline__ uint64_t h1_block_scan(uint64_t x, uint64_t *s_warp, uint64_t &total) {
+    constexpr int NW = kH1Threads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = lane < NW ? s_warp[lane] : 0;
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < NW) s_warp[lane] = wi - w;
+        if (lane == NW - 1) s_warp[NW] = wi;
+    }
+    __syncthreads();
+    total = s_warp[NW];
+    const uint64_t r = inc - x + s_warp[warp];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kH1Threads) k_h1_scan_blocks(const uint64_t *in, int64_t len, uint64_t *out,
+                                                               uint64_t *bsum) {
+    __shared__ uint64_t s_warp[kH1Threads / 32 + 1];
+    const int64_t i0 = int64_t(blockIdx.x) * kH1ScanItems + int64_t(threadIdx.x) * 4;
+    uint64_t x[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        x[q] = i0 + q < len ? in[i0 + q] : 0;
+        sum += x[q];
+    }
+    uint64_t tot;
+    uint64_t run = h1_block_scan(sum, s_warp, tot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (i0 + q < len) out[i0 + q] = run;
+        run += x[q];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of the block sums in place; bsum[blocks] = total.
+__global__ void __launch_bounds__(kH1Threads) k_h1_scan_sums(uint64_t *bsum, int64_t blocks) {
+    __shared__ uint64_t s_warp[kH1Threads / 32 + 1];
+    __shared__ uint64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < blocks; b0 += kH1Threads) {
+        const int64_t b = b0 + threadIdx.x;
+        const uint64_t x = b < blocks ? bsum[b] : 0;
+        uint64_t tot;
+        const uint64_t r = h1_block_scan(x, s_warp, tot);
+        const uint64_t carry = s_carry;
+        if (b < blocks) bsum[b] = carry + r;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blocks] = s_carry;
+}
+
+__global__ void __launch_bounds__(kH1Threads) k_h1_scan_add(uint64_t *out, int64_t len, const uint64_t *bsum,
+                                                            int64_t blocks) {
+    const int64_t i0 = int64_t(blockIdx.x) * kH1ScanItems + int64_t(threadIdx.x) * 4;
+    const uint64_t add = bsum[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (i0 + q < len) out[i0 + q] += add;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = bsum[blocks];
+}
+
+static cudaError_t h1_scan(const uint64_t *in, int64_t len, uint64_t *out, uint64_t *bsum, cudaStream_t s) {
+    const int64_t blocks = (len + kH1ScanItems - 1) / kH1ScanItems;
+    if (blocks == 0) return cudaMemsetAsync(out, 0, sizeof(uint64_t), s);
+    k_h1_scan_blocks<<<unsigned(blocks), kH1Threads, 0, s>>>(in, len, out, bsum);
+    k_h1_scan_sums<<<1, kH1Threads, 0, s>>>(bsum, blocks);
+    k_h1_scan_add<<<unsigned(blocks), kH1Threads, 0, s>>>(out, len, bsum, blocks);
+    return cudaGetLastError();
 }
 
 // -------------------------------------------------------------- step 3 ---
-// Apparent pairs: the first triangle of each diameter owns it.
-__global__ void k_h1_apparent(const uint64_t *tk0, const uint64_t *tk1, const Header *tsort, int64_t T,
-                              int32_t *own_tri, int32_t *pair_low) {
-    const uint64_t *tkey = (make_plan(tsort).passes & 1) ? tk1 : tk0;
-    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < T; j += int64_t(gridDim.x) * blockDim.x) {
-        const uint64_t d = tkey[j];
-        if (j == 0 || tkey[j - 1] != d) {
-            own_tri[d] = int32_t(j);
-            pair_low[j] = int32_t(d);
+// The positions of the edges that are the diameter of no triangle, in order
+// (zpref: exclusive prefix of scan_in).
+__global__ void k_h1_zlist(const uint64_t *scan_in, const uint64_t *zpref, int64_t m, uint32_t *zlist) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m; p += int64_t(gridDim.x) * blockDim.x)
+        if (scan_in[p]) zlist[zpref[p]] = uint32_t(p);
+}
+
+// Kruskal over the listed edges in order (one thread; union-find with path
+// halving in shared memory): an edge that joins two trees is a spanning-
+// forest edge (tfirst = -2: its column is cleared), the others are positive
+// and go to rlist in order.  A full simplex's forest has n-1 edges.
+__global__ void __launch_bounds__(256) k_h1_forest(const uint32_t *vals0, const uint32_t *vals1, const Header *esort,
+                                                   const uint32_t *zlist, const uint64_t *zpref, int64_t m, int64_t n,
+                                                   int32_t *tfirst, uint32_t *rlist, H1Counters *c, Header *h) {
+    __shared__ uint16_t s_par[kH1MaxN];
+    const uint32_t *vals = (make_plan(esort).passes & 1) ? vals1 : vals0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s_par[i] = uint16_t(i);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    auto find = [&](uint32_t x) {
+        while (s_par[x] != x) {
+            s_par[x] = s_par[s_par[x]];
+            x = s_par[x];
+        }
+        return x;
+    };
+    const uint64_t Z = zpref[m];
+    uint64_t forest = 0, k = 0;
+    for (uint64_t z = 0; z < Z; ++z) {
+        const uint32_t p = zlist[z];
+        uint32_t a, b;
+        if (!h1_uv(vals, p, n, a, b)) continue;
+        const uint32_t ra = find(a), rb = find(b);
+        if (ra != rb) {
+            s_par[ra] = uint16_t(rb);
+            tfirst[p] = -2;
+            ++forest;
         } else {
-            pair_low[j] = -1;
+            rlist[k++] = p;
+        }
+    }
+    c->zero = Z;
+    c->forest = forest;
+    c->reduced = k;
+    if (int64_t(forest) != n - 1) set_status(h, PH0_EINTERNAL);
+}
+
+// -------------------------------------------------------------- step 4 ---
+struct H1Reduce {
+    int64_t n;
+    const uint32_t *vals0, *vals1;
+    const Header *esort;
+    const uint32_t *P;
+    const int32_t *tfirst;
+    const uint32_t *rlist;
+    int32_t *head;             // [m] first claim of each diameter position, -1: none
+    uint32_t *claims;          // [m] claims per diameter position
+    uint64_t *node_key;        // claims: the pivot triangle,
+    uint32_t *node_pos;        //   the claiming column's edge position,
+    int32_t *node_next;        //   the next claim of the same diameter,
+    uint32_t *node_within;     //   the pivot's rank among its diameter's triangles
+    uint32_t *own_node;        // [m] the claim of each reduced column
+    uint64_t *own_off;         // [m] its reduced column in the pool
+    uint32_t *own_len;
+    uint64_t *col_a, *col_b, *col_m;
+    int64_t col_cap;
+    uint64_t *pool;
+    int64_t pool_cap;
+    H1Counters *c;
+    Header *h;
+};
+
+// The coboundary of edge {a, b} at position p, sorted, into s_keys: n-2 keys
+// (the rest of the power of two padded with ~0).  All threads.
+__device__ void h1_cobound(const uint32_t *P, int64_t n, uint32_t a, uint32_t b, uint32_t p, uint64_t *s_keys) {
+    int n2 = 2;
+    while (n2 < n) n2 <<= 1;
+    const uint32_t *Pa = P + int64_t(a) * n, *Pb = P + int64_t(b) * n;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        uint64_t k = ~0ull;
+        if (i < n && uint32_t(i) != a && uint32_t(i) != b) {
+            uint32_t d = p;
+            const uint32_t x = Pa[i], y = Pb[i];
+            d = x > d ? x : d;
+            d = y > d ? y : d;
+            k = h1_key(d, a, b, uint32_t(i));
+        }
+        s_keys[i] = k;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = s_keys[i], y = s_keys[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((x > y) == up) {
+                        s_keys[i] = y;
+                        s_keys[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
 }
 
-// -------------------------------------------------------------- step 4 ---
-struct H1Counters {
-    unsigned long long pool_used;
-    unsigned long long bars;
-    uint32_t active[2];
-    uint32_t rounds;
-    uint32_t max_len;
-};
-
-struct H1Args {
-    int64_t n, m, T, w0, w1;
-    const uint32_t *posof;
-    const uint64_t *tk0, *tk1;
-    const uint32_t *tv0, *tv1;
-    const Header *tsort;
-    const int32_t *own_tri;
-    uint32_t *own_off, *own_len;
-    int32_t *pair_low;
-    uint32_t *slots, *slen;
-    int cap;
-    uint32_t *pool;
-    unsigned long long pool_cap;
-    H1Counters *c;
-    Header *h;     // status (the call's header)
-    Header *bh;    // grid barrier
-};
-
-__global__ void __launch_bounds__(kH1Threads, 1) k_h1_window(H1Args A) {
-    __shared__ int s_ok;
-    __shared__ uint32_t s_warp[kH1Threads / 32];
-    __shared__ int32_t s_carry;
-    const bool odd = make_plan(A.tsort).passes & 1;
-    const uint32_t *tval = odd ? A.tv1 : A.tv0;
-    const int tid = threadIdx.x;
-    const int64_t W = A.w1 - A.w0;
-    const int64_t gtid = int64_t(blockIdx.x) * kH1Threads + tid, gstride = int64_t(gridDim.x) * kH1Threads;
-    const int cap = A.cap;
-    auto slot = [&](int64_t i, uint32_t half) { return A.slots + (size_t(i) * 2 + half) * size_t(cap); };
-
-    // A: the window's columns that are not apparent owners
-    for (int64_t i = gtid; i < W; i += gstride) {
-        const int64_t j = A.w0 + i;
-        if (A.pair_low[j] >= 0) {
-            A.slen[i] = 0;
-            continue;
-        }
-        uint32_t u, v, w, e[3];
-        h1_unpack(tval[j], u, v, w);
-        h1_tri_edges(A.posof, A.n, u, v, w, e);
-        uint32_t *col = slot(i, 0);
-        col[0] = e[0];
-        col[1] = e[1];
-        col[2] = e[2];
-        A.slen[i] = 3;
+// Merge-path split: the number of items of A among the first d of the merge
+// of A and B (ascending; A first among equal keys).
+__device__ __forceinline__ int64_t h1_split(const uint64_t *A, int64_t LA, const uint64_t *B, int64_t LB, int64_t d) {
+    int64_t lo = d > LB ? d - LB : 0, hi = d < LA ? d : LA;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d - 1 - mid]) lo = mid + 1;
+        else hi = mid;
     }
-    if (!grid_barrier(A.bh, &s_ok, kSpinLimit)) return;
+    return lo;
+}
 
-    for (uint32_t round = 0;; ++round) {
-        // B: add the columns of final owners of the low, while there is one
-        if (blockIdx.x == 0 && tid == 0) A.c->active[round & 1] = 0;
-        uint32_t longest = 0;
-        for (int64_t i = gtid; i < W; i += gstride) {
-            uint32_t s = __ldcg(A.slen + i);  // CTA 0 may have finalized it
-            int len = int(s & 0x7fffffffu);
-            if (len == 0) continue;
-            uint32_t half = s >> 31;
-            const uint32_t *col = slot(i, half);
-            for (;;) {
-                const uint32_t L = col[len - 1];
-                uint32_t tri3[3];
-                const uint32_t *oc;
-                int olen;
-                const int32_t ot = A.own_tri[L];
-                if (ot >= 0) {
-                    uint32_t u, v, w;
-                    h1_unpack(tval[ot], u, v, w);
-                    h1_tri_edges(A.posof, A.n, u, v, w, tri3);
-                    oc = tri3;
-                    olen = 3;
-                } else if (__ldcg(A.own_off + L) != 0xffffffffu) {  // written by CTA 0 in an earlier round
-                    oc = A.pool + __ldcg(A.own_off + L);
-                    olen = int(__ldcg(A.own_len + L));
+// C = A (+) B over F2: the symmetric difference of two ascending lists of
+// distinct keys (M: room for LA + LB, the merge with the pairs of equal keys
+// side by side); returns its length, or -1 (nothing written to C) above cap.
+// All threads.
+__device__ int64_t h1_symdiff(const uint64_t *A, int64_t LA, const uint64_t *B, int64_t LB, uint64_t *M,
+                              uint64_t *C, int64_t cap, uint64_t *s_warp) {
+    const int64_t total = LA + LB, T = blockDim.x, t = threadIdx.x;
+    const int64_t d0 = total * t / T, d1 = total * (t + 1) / T;
+    int64_t i = h1_split(A, LA, B, LB, d0), j = d0 - i;
+    for (int64_t k = d0; k < d1; ++k) {
+        if (j >= LB || (i < LA && A[i] <= B[j])) M[k] = A[i++];
+        else M[k] = B[j++];
+    }
+    __syncthreads();
+    auto keep = [&](int64_t k) {
+        const uint64_t x = M[k];
+        return !((k > 0 && M[k - 1] == x) || (k + 1 < total && M[k + 1] == x));
+    };
+    uint64_t cnt = 0;
+    for (int64_t k = d0; k < d1; ++k) cnt += keep(k) ? 1u : 0u;
+    uint64_t kept;
+    uint64_t off = h1_block_scan(cnt, s_warp, kept);
+    if (int64_t(kept) > cap) return -1;
+    for (int64_t k = d0; k < d1; ++k)
+        if (keep(k)) C[off++] = M[k];
+    __syncthreads();
+    return int64_t(kept);
+}
+
+// One CTA: the listed columns from the latest edge down (see the top).
+__global__ void __launch_bounds__(kH1Threads) k_h1_reduce(H1Reduce R) {
+    __shared__ uint64_t s_keys[kH1MaxN];
+    __shared__ uint64_t s_warp[kH1Threads / 32 + 1];
+    __shared__ int32_t s_owner, s_app, s_err;
+    __shared__ uint32_t s_node;
+    const uint32_t *vals = (make_plan(R.esort).passes & 1) ? R.vals1 : R.vals0;
+    const int tid = threadIdx.x;
+    const int64_t n = R.n;
+    const int64_t K = int64_t(R.c->reduced);
+    uint64_t *A = R.col_a, *C = R.col_b;
+    unsigned long long adds = 0, maxlen = 0, pool_used = 0, nodes = 0;
+    if (tid == 0) s_err = 0;
+    __syncthreads();
+    for (int64_t k = K - 1; k >= 0; --k) {
+        const uint32_t p = R.rlist[k];
+        uint32_t a, b;
+        h1_uv(vals, p, n, a, b);  // listed from checked records
+        h1_cobound(R.P, n, a, b, p, s_keys);
+        int64_t LA = n - 2;
+        for (int64_t i = tid; i < LA; i += blockDim.x) A[i] = s_keys[i];
+        __syncthreads();
+        uint64_t piv = 0;
+        for (;;) {
+            if (LA == 0) {  // every positive column keeps a pivot: a bug if not
+                if (tid == 0) s_err = PH0_EINTERNAL;
+                break;
+            }
+            piv = A[0];
+            if (tid == 0) {
+                const uint32_t dp = h1_key_dpos(piv);
+                uint32_t a2, b2;
+                if (!h1_uv(vals, dp, n, a2, b2)) s_err = PH0_EINTERNAL;
+                if (adds >= kH1MaxAdditions) s_err = PH0_ETOOBIG;
+                int32_t owner = -1, app = 0;
+                const int32_t f = R.tfirst[dp];
+                if (f >= 0 && h1_key(dp, a2, b2, uint32_t(f)) == piv) {
+                    owner = int32_t(dp);
+                    app = 1;
                 } else {
-                    break;  // no final owner: wait for the ordering below
-                }
-                uint32_t *out = slot(i, half ^ 1u);
-                const int k = h1_symdiff(col, len, oc, olen, out, cap, ot < 0);
-                if (k < 0) {  // the column outgrew its slot
-                    set_status(A.h, PH0_ETOOBIG);
-                    atomicExch(&A.bh->abort, 1);
-                    len = 0;
-                    break;
-                }
-                half ^= 1u;
-                col = out;
-                len = k;
-                longest = uint32_t(len) > longest ? uint32_t(len) : longest;
-                if (len == 0) break;
-            }
-            A.slen[i] = uint32_t(len) | (half << 31);
-        }
-        if (longest) atomicMax(&A.c->max_len, longest);
-        if (!grid_barrier(A.bh, &s_ok, kSpinLimit)) return;
-
-        // C (one CTA): in position order, a column whose low exceeds every
-        // earlier active column's low becomes the final owner of that low
-        if (blockIdx.x == 0) {
-            if (tid == 0) s_carry = -1;
-            __syncthreads();
-            uint32_t left = 0;
-            for (int64_t base = 0; base < W; base += kH1Threads) {
-                const int64_t i = base + tid;
-                int32_t low = -1;
-                uint32_t s = 0;
-                if (i < W) {
-                    s = __ldcg(A.slen + i);  // written by other CTAs in part B
-                    const int len = int(s & 0x7fffffffu);
-                    if (len) low = int32_t(__ldcg(slot(i, s >> 31) + (len - 1)));
-                }
-                if (!__syncthreads_or(low >= 0)) continue;  // no column left here: the carry stays
-                // inclusive max over the block, position order
-                int32_t inc = low;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if ((tid & 31) >= o) inc = y > inc ? y : inc;
-                }
-                if ((tid & 31) == 31) s_warp[tid >> 5] = uint32_t(inc);
-                __syncthreads();
-                int32_t before = s_carry;
-                for (int wp = 0; wp < (tid >> 5); ++wp) {
-                    const int32_t y = int32_t(s_warp[wp]);
-                    before = y > before ? y : before;
-                }
-                {
-                    const int32_t y = __shfl_up_sync(0xffffffffu, inc, 1);
-                    if ((tid & 31) >= 1) before = y > before ? y : before;
-                }
-                if (low >= 0) {
-                    if (before < low) {
-                        const int len = int(s & 0x7fffffffu);
-                        const uint32_t *col = slot(i, s >> 31);
-                        const unsigned long long off = atomicAdd(&A.c->pool_used, (unsigned long long)len);
-                        if (off + len > A.pool_cap) {
-                            set_status(A.h, PH0_ETOOBIG);
-                            atomicExch(&A.bh->abort, 1);
-                        } else {
-                            for (int q = 0; q < len; ++q) A.pool[off + q] = __ldcg(col + q);
-                            A.own_len[low] = uint32_t(len);
-                            A.own_off[low] = uint32_t(off);
-                            A.pair_low[A.w0 + i] = low;
+                    for (int32_t q = R.head[dp]; q >= 0; q = R.node_next[q])
+                        if (R.node_key[q] == piv) {
+                            owner = int32_t(R.node_pos[q]);
+                            break;
                         }
-                        A.slen[i] = 0;
-                    } else {
-                        ++left;
-                    }
                 }
-                __syncthreads();
-                if (tid == kH1Threads - 1) {
-                    const int32_t tot = before > inc ? before : inc;
-                    s_carry = tot > s_carry ? tot : s_carry;
-                }
-                __syncthreads();
+                s_owner = owner;
+                s_app = app;
             }
-            if (left) atomicAdd(&A.c->active[round & 1], left);
-            if (tid == 0) atomicAdd(&A.c->rounds, 1u);
+            __syncthreads();
+            const int32_t owner = s_owner;
+            const bool app = s_app != 0;
+            const bool stop = s_err != 0;
+            __syncthreads();
+            if (stop || owner < 0) break;
+            const uint64_t *B;
+            int64_t LB;
+            if (app) {
+                uint32_t a2, b2;
+                h1_uv(vals, owner, n, a2, b2);  // checked above as the pivot's diameter edge
+                h1_cobound(R.P, n, a2, b2, uint32_t(owner), s_keys);
+                B = s_keys;
+                LB = n - 2;
+            } else {
+                B = R.pool + R.own_off[owner];
+                LB = R.own_len[owner];
+            }
+            const int64_t LC = h1_symdiff(A, LA, B, LB, R.col_m, C, R.col_cap, s_warp);
+            if (LC < 0) {
+                if (tid == 0) s_err = PH0_ETOOBIG;
+                __syncthreads();
+                break;
+            }
+            uint64_t *t = A;
+            A = C;
+            C = t;
+            LA = LC;
+            ++adds;
+            if (uint64_t(LA) > maxlen) maxlen = uint64_t(LA);
         }
-        if (!grid_barrier(A.bh, &s_ok, kSpinLimit)) return;
-        if (ld_volatile(&A.c->active[round & 1]) == 0 || ld_volatile(&A.bh->abort)) break;
+        __syncthreads();
+        if (s_err) break;
+        // claim the pivot: a node in the list of its diameter position
+        const uint32_t dp = h1_key_dpos(piv);
+        uint32_t a2, b2, u, v, w;
+        h1_uv(vals, dp, n, a2, b2);  // checked above
+        h1_key_uvw(piv, u, v, w);
+        const uint32_t wt = (u != a2 && u != b2) ? u : ((v != a2 && v != b2) ? v : w);
+        if (tid == 0) {
+            const uint32_t q = uint32_t(nodes++);
+            R.node_key[q] = piv;
+            R.node_pos[q] = p;
+            R.node_next[q] = R.head[dp];
+            R.head[dp] = int32_t(q);
+            R.claims[dp] += 1;
+            R.own_node[p] = q;
+            s_node = q;
+        }
+        // its rank among the triangles of diameter dp: third vertices before wt
+        const uint32_t *Pa = R.P + int64_t(a2) * n, *Pb = R.P + int64_t(b2) * n;
+        uint64_t cnt = 0;
+        for (uint32_t x = tid; x < wt; x += blockDim.x) cnt += (Pa[x] < dp && Pb[x] < dp) ? 1u : 0u;
+        uint64_t within;
+        h1_block_scan(cnt, s_warp, within);
+        if (tid == 0) R.node_within[s_node] = uint32_t(within);
+        // keep the reduced column for the columns below
+        if (int64_t(pool_used) + LA > R.pool_cap) {
+            if (tid == 0) s_err = PH0_ETOOBIG;
+            __syncthreads();
+            break;
+        }
+        for (int64_t i = tid; i < LA; i += blockDim.x) R.pool[pool_used + i] = A[i];
+        if (tid == 0) {
+            R.own_off[p] = pool_used;
+            R.own_len[p] = uint32_t(LA);
+        }
+        pool_used += uint64_t(LA);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        R.c->additions = adds;
+        R.c->max_len = maxlen;
+        R.c->pool_used = pool_used;
+        R.c->nodes = nodes;
+        if (s_err) set_status(R.h, s_err);
     }
 }
 
 // -------------------------------------------------------------- step 5 ---
-__global__ void k_h1_count(const int32_t *pair_low, int64_t T, uint32_t *cnt) {
-    __shared__ uint32_t s_sum;
-    if (threadIdx.x == 0) s_sum = 0;
-    __syncthreads();
-    const int64_t base = int64_t(blockIdx.x) * kH1ChunkTris;
-    uint32_t c = 0;
-    for (int q = threadIdx.x; q < kH1ChunkTris; q += blockDim.x) {
-        const int64_t j = base + q;
-        c += (j < T && pair_low[j] >= 0) ? 1u : 0u;
-    }
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_sum, c);
-    __syncthreads();
-    if (threadIdx.x == 0) cnt[blockIdx.x] = s_sum;
+// scan_in[p] = (triangles of diameter p) << 24 | (claims at p), whose
+// exclusive prefix gives, at p, the rank of p's first triangle in triangle
+// order (high part) and the claims of earlier diameters (low 24 bits).
+__global__ void k_h1_pack(const uint32_t *tcount, const uint32_t *claims, int64_t m, uint64_t *scan_in) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m; p += int64_t(gridDim.x) * blockDim.x)
+        scan_in[p] = (uint64_t(tcount[p]) << 24) | claims[p];
 }
 
-// Exclusive scan of the chunk counts in place (one CTA); total to *total.
-__global__ void k_h1_scan(uint32_t *cnt, int64_t chunks, unsigned long long *total) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < chunks; base += blockDim.x) {
-        const int64_t i = base + tid;
-        const uint32_t x = i < chunks ? cnt[i] : 0u;
-        uint32_t inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+// The bar of every positive edge at its place in triangle order: before the
+// bar of apparent edge p come the apparent pairs of earlier edges (p less the
+// edges with no triangle before p) and the claims of earlier diameters; before
+// a claim at diameter dp come also dp's apparent pair and the claims at dp
+// with a smaller rank.
+__global__ void k_h1_emit(const uint64_t *ek0, const uint64_t *ek1, const uint32_t *ev0, const uint32_t *ev1,
+                          const Header *esort, const uint32_t *a_of, const int32_t *tfirst, const uint64_t *zpref,
+                          const uint64_t *tpref, const uint32_t *own_node, const uint64_t *node_key,
+                          const uint32_t *node_within, const int32_t *head, const int32_t *node_next, int64_t m,
+                          int64_t n, int64_t nbars, ph0_h1bar *bars, H1Counters *c) {
+    const bool odd = make_plan(esort).passes & 1;
+    const uint64_t *ekey = odd ? ek1 : ek0;
+    const uint32_t *eval = odd ? ev1 : ev0;
+    unsigned long long written = 0;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m; p += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t f = tfirst[p];
+        if (f == -2) continue;  // a spanning-forest edge
+        uint32_t a, b;
+        if (!h1_uv(eval, p, n, a, b)) continue;
+        uint64_t tk, rank, out;
+        if (f >= 0) {
+            tk = h1_key(uint64_t(p), a, b, uint32_t(f));
+            rank = tpref[p] >> 24;
+            out = (uint64_t(p) - zpref[p]) + (tpref[p] & 0xffffffu);
+        } else {
+            const uint32_t q = own_node[p];
+            if (q == kH1NoPos) continue;  // the reduction stopped early (its status says why)
+            tk = node_key[q];
+            const uint32_t dp = h1_key_dpos(tk), wq = node_within[q];
+            rank = (tpref[dp] >> 24) + wq;
+            uint64_t before = 0;
+            for (int32_t r = head[dp]; r >= 0; r = node_next[r]) before += node_within[r] < wq ? 1u : 0u;
+            out = (uint64_t(dp) - zpref[dp]) + 1 + (tpref[dp] & 0xffffffu) + before;
         }
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        uint32_t before = s_carry;
-        for (int w = 0; w < warp; ++w) before += s_warp[w];
-        if (i < chunks) cnt[i] = before + inc - x;
-        __syncthreads();
-        if (tid == int(blockDim.x) - 1) s_carry = before + inc;
-        __syncthreads();
+        const uint32_t dp = h1_key_dpos(tk);
+        uint32_t tu, tv, tw;
+        h1_key_uvw(tk, tu, tv, tw);
+        if (int64_t(out) >= nbars) continue;  // only with inconsistent counts: the host sees the bar count
+        ph0_h1bar bar;
+        bar.eu = int32_t(a);
+        bar.ev = int32_t(b);
+        bar.tu = int32_t(tu);
+        bar.tv = int32_t(tv);
+        bar.tw = int32_t(tw);
+        bar.birth_a = a_of[p];
+        bar.death_a = a_of[dp];
+        bar._pad = 0;
+        bar.birth_order = p;
+        bar.death_order = int64_t(dp);
+        bar.death_rank = int64_t(rank);
+        bar.birth_sq = __longlong_as_double((long long)ekey[p]);
+        bar.death_sq = __longlong_as_double((long long)ekey[dp]);
+        bars[out] = bar;
+        ++written;
     }
-    if (tid == 0) *total = s_carry;
-}
-
-// The bars of one chunk of triangles, in triangle order.
-__global__ void k_h1_emit(const int32_t *pair_low, int64_t T, const uint32_t *cnt, const uint64_t *tk0,
-                          const uint64_t *tk1, const uint32_t *tv0, const uint32_t *tv1, const Header *tsort,
-                          const uint64_t *ek0, const uint64_t *ek1, const uint32_t *ev0, const uint32_t *ev1,
-                          const Header *esort, const uint32_t *a_of, int64_t n, int64_t nbars, ph0_h1bar *bars) {
-    __shared__ uint32_t s_warp[kH1Threads / 32];
-    __shared__ uint32_t s_carry;
-    const bool todd = make_plan(tsort).passes & 1, eodd = make_plan(esort).passes & 1;
-    const uint64_t *tkey = todd ? tk1 : tk0;
-    const uint32_t *tval = todd ? tv1 : tv0;
-    const uint64_t *ekey = eodd ? ek1 : ek0;
-    const uint32_t *eval = eodd ? ev1 : ev0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = cnt[blockIdx.x];
-    __syncthreads();
-    const int64_t base = int64_t(blockIdx.x) * kH1ChunkTris;
-    for (int q0 = 0; q0 < kH1ChunkTris; q0 += kH1Threads) {
-        const int64_t j = base + q0 + tid;
-        const bool has = j < T && pair_low[j] >= 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, has);
-        if (lane == 0) s_warp[warp] = __popc(bal);
-        __syncthreads();
-        uint32_t before = s_carry;
-        for (int w = 0; w < warp; ++w) before += s_warp[w];
-        before += __popc(bal & ((1u << lane) - 1u));
-        if (has && int64_t(before) < nbars) {
-            const uint32_t p = uint32_t(pair_low[j]);
-            const uint32_t dpos = uint32_t(tkey[j]);
-            uint32_t eu, ev, tu, tv, tw;
-            record_uv(eval[p], false, n, eu, ev);
-            h1_unpack(tval[j], tu, tv, tw);
-            ph0_h1bar b;
-            b.eu = int32_t(eu);
-            b.ev = int32_t(ev);
-            b.tu = int32_t(tu);
-            b.tv = int32_t(tv);
-            b.tw = int32_t(tw);
-            b.birth_a = a_of[p];
-            b.death_a = a_of[dpos];
-            b._pad = 0;
-            b.birth_order = int64_t(p);
-            b.death_order = int64_t(dpos);
-            b.death_rank = j;
-            b.birth_sq = __longlong_as_double((long long)ekey[p]);
-            b.death_sq = __longlong_as_double((long long)ekey[dpos]);
-            bars[before] = b;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t tot = 0;
-            for (int w = 0; w < kH1Threads / 32; ++w) tot += s_warp[w];
-            s_carry += tot;
-        }
-        __syncthreads();
-    }
+    if (written) atomicAdd(&c->bars, written);
 }
 
 // ------------------------------------------------------------------ host ---
 int sm_count();
-cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s, int top_bits,
-                             int64_t sorted_edges, const int32_t *gate);
-cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s, const int32_t *gate);
-cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
-                               cudaStream_t s, bool persist);
 
 // Steps 1-5 of the first homology on a workspace whose dimension-0 part
 // holds the sorted edges (buffer by esort's plan) and the de-duplication
-// chunk prefixes; bars: n(n-1)/2 - (n-1) entries.  Asynchronous on s.
+// chunk prefixes; bars: n(n-1)/2 - (n-1) entries.  Asynchronous on s;
+// after_scan / after_reduce (may be null) are recorded after steps 2 and 4.
 cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, const uint64_t *ek1,
                    const uint32_t *ev0, const uint32_t *ev1, const Header *esort, const uint32_t *cpref,
-                   Header *h, ph0_h1bar *bars, cudaStream_t s, cudaEvent_t after_sort, cudaEvent_t after_reduce) {
-    const int64_t m = n_edges(n), T = H.T;
-    Header *th = at<Header>(ws, H.thdr);
+                   Header *h, ph0_h1bar *bars, cudaStream_t s, cudaEvent_t after_scan, cudaEvent_t after_reduce) {
+    const int64_t m = n_edges(n);
     H1Counters *c = at<H1Counters>(ws, H.cnt);
-    uint32_t *a_of = at<uint32_t>(ws, H.aof), *posof = at<uint32_t>(ws, H.posof);
-    uint64_t *tk0 = at<uint64_t>(ws, H.tkey[0]), *tk1 = at<uint64_t>(ws, H.tkey[1]);
-    uint32_t *tv0 = at<uint32_t>(ws, H.tval[0]), *tv1 = at<uint32_t>(ws, H.tval[1]);
-    int32_t *own_tri = at<int32_t>(ws, H.own_tri), *pair_low = at<int32_t>(ws, H.pair_low);
-    uint32_t *own_off = at<uint32_t>(ws, H.own_off), *own_len = at<uint32_t>(ws, H.own_len);
-    cudaError_t e = cudaMemsetAsync(th, 0, kHeaderBytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, sizeof(H1Counters), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(own_tri, 0xff, 4 * size_t(m), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(own_off, 0xff, 4 * size_t(m), s);
-    if (e != cudaSuccess || T == 0) return e;
+    uint32_t *a_of = at<uint32_t>(ws, H.aof), *posof = at<uint32_t>(ws, H.posof), *P = at<uint32_t>(ws, H.pmat);
+    uint32_t *tcount = at<uint32_t>(ws, H.tcount);
+    int32_t *tfirst = at<int32_t>(ws, H.tfirst);
+    uint64_t *scan_in = at<uint64_t>(ws, H.scan_in), *zpref = at<uint64_t>(ws, H.zpref);
+    uint64_t *tpref = at<uint64_t>(ws, H.tpref), *bsum = at<uint64_t>(ws, H.bsum);
+    uint32_t *zlist = at<uint32_t>(ws, H.zlist), *rlist = at<uint32_t>(ws, H.rlist);
+    int32_t *head = at<int32_t>(ws, H.head);
+    uint32_t *claims = at<uint32_t>(ws, H.claims);
+    cudaError_t e = cudaMemsetAsync(c, 0, sizeof(H1Counters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(head, 0xff, 4 * size_t(m + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(claims, 0, 4 * size_t(m + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(at<uint32_t>(ws, H.own_node), 0xff, 4 * size_t(m + 1), s);
+    if (e != cudaSuccess || H.T == 0) return e;
     const int grid = sm_count() * 8;
-    // 1. a and the position of every edge; 2. the triangles, sorted
+    // 1. a and the position of every edge, the position matrix
     k_h1_aof<<<grid, 256, 0, s>>>(ek0, ek1, esort, m, cpref, a_of);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_h1_posof<<<grid, 256, 0, s>>>(ev0, ev1, esort, m, n, posof);
+    k_h1_pmat<<<grid, 256, 0, s>>>(posof, n, P);
+    // 2. the triangles of each diameter; the edges with none, in order
+    k_h1_edges<<<grid, 256, 0, s>>>(ev0, ev1, esort, m, n, P, tcount, tfirst, scan_in);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_h1_tris<<<grid, 256, 0, s>>>(posof, n, m, tk0, tv0);
+    if ((e = h1_scan(scan_in, m, zpref, bsum, s)) != cudaSuccess) return e;
+    if (after_scan && (e = cudaEventRecord(after_scan, s)) != cudaSuccess) return e;
+    // 3. the spanning forest; 4. the other columns
+    k_h1_zlist<<<grid, 256, 0, s>>>(scan_in, zpref, m, zlist);
+    k_h1_forest<<<1, 256, 0, s>>>(ev0, ev1, esort, zlist, zpref, m, n, tfirst, rlist, c, h);
+    H1Reduce R;
+    R.n = n;
+    R.vals0 = ev0;
+    R.vals1 = ev1;
+    R.esort = esort;
+    R.P = P;
+    R.tfirst = tfirst;
+    R.rlist = rlist;
+    R.head = head;
+    R.claims = claims;
+    R.node_key = at<uint64_t>(ws, H.node_key);
+    R.node_pos = at<uint32_t>(ws, H.node_pos);
+    R.node_next = at<int32_t>(ws, H.node_next);
+    R.node_within = at<uint32_t>(ws, H.node_within);
+    R.own_node = at<uint32_t>(ws, H.own_node);
+    R.own_off = at<uint64_t>(ws, H.own_off);
+    R.own_len = at<uint32_t>(ws, H.own_len);
+    R.col_a = at<uint64_t>(ws, H.col_a);
+    R.col_b = at<uint64_t>(ws, H.col_b);
+    R.col_m = at<uint64_t>(ws, H.col_m);
+    R.col_cap = H.col_cap;
+    R.pool = at<uint64_t>(ws, H.pool);
+    R.pool_cap = H.pool_cap;
+    R.c = c;
+    R.h = h;
+    k_h1_reduce<<<1, kH1Threads, 0, s>>>(R);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_sort_init(th, at<uint64_t>(ws, H.tlook[0]), H.ttiles, s, kDefaultTopBits, T, nullptr);
-    if (e == cudaSuccess) e = launch_keystats(tk0, T, th, s, nullptr);
-    if (e == cudaSuccess)
-        e = launch_sort_passes(tk0, tk1, tv0, tv1, T, at<uint64_t>(ws, H.tlook[0]), at<uint64_t>(ws, H.tlook[1]), th,
-                               s, false);
-    if (e == cudaSuccess && after_sort) e = cudaEventRecord(after_sort, s);
-    if (e != cudaSuccess) return e;
-    // 3. apparent pairs; 4. the other columns, window by window
-    k_h1_apparent<<<grid, 256, 0, s>>>(tk0, tk1, th, T, own_tri, pair_low);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_h1_window, kH1Threads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int wgrid = sm_count() * (per_sm > 2 ? 2 : per_sm);
-    H1Args A;
-    A.n = n;
-    A.m = m;
-    A.T = T;
-    A.posof = posof;
-    A.tk0 = tk0;
-    A.tk1 = tk1;
-    A.tv0 = tv0;
-    A.tv1 = tv1;
-    A.tsort = th;
-    A.own_tri = own_tri;
-    A.own_off = own_off;
-    A.own_len = own_len;
-    A.pair_low = pair_low;
-    A.slots = at<uint32_t>(ws, H.slots);
-    A.slen = at<uint32_t>(ws, H.slen);
-    A.cap = kH1Cap;
-    A.pool = at<uint32_t>(ws, H.pool);
-    A.pool_cap = (unsigned long long)H.pool_cap;
-    A.c = c;
-    A.h = h;
-    A.bh = th;
-    for (int64_t w0 = 0; w0 < T; w0 += H.W) {
-        A.w0 = w0;
-        A.w1 = w0 + H.W < T ? w0 + H.W : T;
-        H1Args args = A;
-        void *params[] = {&args};
-        e = cudaLaunchCooperativeKernel((const void *)k_h1_window, dim3(wgrid), dim3(kH1Threads), params, 0, s);
-        if (e != cudaSuccess) return e;
-    }
     if (after_reduce && (e = cudaEventRecord(after_reduce, s)) != cudaSuccess) return e;
-    // 5. the bars in triangle order
-    uint32_t *ccount = at<uint32_t>(ws, H.ccount);
-    k_h1_count<<<unsigned(H.chunks), 256, 0, s>>>(pair_low, T, ccount);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_h1_scan<<<1, 1024, 0, s>>>(ccount, H.chunks, &c->bars);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_h1_emit<<<unsigned(H.chunks), kH1Threads, 0, s>>>(pair_low, T, ccount, tk0, tk1, tv0, tv1, th, ek0, ek1, ev0,
-                                                        ev1, esort, a_of, n, m - (n - 1), bars);
+    // 5. ranks in triangle order, the bars
+    k_h1_pack<<<grid, 256, 0, s>>>(tcount, claims, m, scan_in);
+    if ((e = h1_scan(scan_in, m, tpref, bsum, s)) != cudaSuccess) return e;
+    k_h1_emit<<<grid, 256, 0, s>>>(ek0, ek1, ev0, ev1, esort, a_of, tfirst, zpref, tpref, R.own_node, R.node_key,
+                                   R.node_within, head, R.node_next, m, n, m - (n - 1), bars, c);
     return cudaGetLastError();
 }
 
-// Counters of the last run_h1 on ws (host copy).
-cudaError_t h1_counters(const void *ws, const H1Layout &H, uint64_t out[5]) {
+// Counters of the last run_h1 on ws (host copy): bars, apparent pairs,
+// reduced columns, additions, longest column, pool keys, and the triangle
+// count from the prefix sums (n(n-1)(n-2)/6 when consistent).
+cudaError_t h1_counters(const void *ws, const H1Layout &H, int64_t n, uint64_t out[7]) {
     H1Counters hc;
     cudaError_t e = cudaMemcpy(&hc, static_cast<const char *>(ws) + H.cnt, sizeof(hc), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return e;
+    const int64_t m = n_edges(n);
+    uint64_t tp = 0;
+    e = cudaMemcpy(&tp, static_cast<const char *>(ws) + H.tpref + 8 * size_t(m), sizeof(tp), cudaMemcpyDeviceToHost);
     out[0] = hc.bars;
-    out[1] = hc.pool_used;
-    out[2] = hc.rounds;
-    out[3] = hc.max_len;
-    int32_t tstatus = 0;  // the triangle sort's header: its status word comes first
-    e = cudaMemcpy(&tstatus, static_cast<const char *>(ws) + H.thdr, sizeof(tstatus), cudaMemcpyDeviceToHost);
-    out[4] = uint64_t(uint32_t(tstatus));
+    out[1] = uint64_t(m) - hc.zero;
+    out[2] = hc.reduced;
+    out[3] = hc.additions;
+    out[4] = hc.max_len;
+    out[5] = hc.pool_used;
+    out[6] = tp >> 24;
     return e;
 }
 

@@ -60,7 +60,7 @@ cudaError_t launch_inf(Header *h, int64_t n, ph0_inf_bar *inf, cudaStream_t s);
 cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, const uint64_t *ek1,
                    const uint32_t *ev0, const uint32_t *ev1, const Header *esort, const uint32_t *cpref,
                    Header *h, ph0_h1bar *bars, cudaStream_t s, cudaEvent_t after_sort, cudaEvent_t after_reduce);
-cudaError_t h1_counters(const void *ws, const H1Layout &H, uint64_t out[5]);
+cudaError_t h1_counters(const void *ws, const H1Layout &H, int64_t n, uint64_t out[7]);
 cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
@@ -255,7 +255,7 @@ const char *ph0_strerror(int status) {
     }
 }
 
-int32_t ph0_abi_version(void) { return 3; }
+int32_t ph0_abi_version(void) { return 4; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
     if (check_sizes(n, d, d, kMaxNWide) != PH0_OK) return 0;
@@ -673,7 +673,7 @@ int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *ba
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
-    // stage events: start | edges | triangles sorted | reduced | end
+    // stage events: start | edges | triangles of each diameter | reduced | end
     cudaEvent_t ev[5] = {};
     int made = 0;
     cudaError_t e = cudaSuccess;
@@ -697,21 +697,23 @@ int ph0_h1(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_h1bar *ba
     float ms[4] = {0, 0, 0, 0};
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
     for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
-    uint64_t cnt[5] = {0, 0, 0, 0, 0};
+    uint64_t cnt[7] = {0, 0, 0, 0, 0, 0, 0};
     int32_t status = PH0_OK;
     if (e == cudaSuccess) e = cudaMemcpy(&status, &h->status, sizeof(status), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nbars > 0) e = h1_counters(ws, H, cnt);
+    if (e == cudaSuccess && nbars > 0) e = h1_counters(ws, H, n, cnt);
     if (e != cudaSuccess) return PH0_ECUDA;
-    if (status == PH0_OK && cnt[4] != 0) status = int32_t(cnt[4]);  // the triangle sort's status
-    if (status == PH0_OK && nbars > 0 && int64_t(cnt[0]) != nbars) status = PH0_EINTERNAL;
+    if (status == PH0_OK && nbars > 0 && (int64_t(cnt[0]) != nbars || int64_t(cnt[6]) != H.T))
+        status = PH0_EINTERNAL;
     if (stats) {
         stats->n_bars = nbars > 0 ? int64_t(cnt[0]) : 0;
-        stats->n_triangles = H.T;
-        stats->pool_entries = int64_t(cnt[1]);
-        stats->rounds = int32_t(cnt[2]);
-        stats->max_column = int32_t(cnt[3]);
+        stats->n_triangles = nbars > 0 ? int64_t(cnt[6]) : H.T;
+        stats->apparent = int64_t(cnt[1]);
+        stats->reduced = int64_t(cnt[2]);
+        stats->additions = int64_t(cnt[3]);
+        stats->max_column = int64_t(cnt[4]);
+        stats->pool_entries = int64_t(cnt[5]);
         stats->edges_ms = ms[0];
-        stats->triangles_ms = ms[1];
+        stats->scan_ms = ms[1];
         stats->reduce_ms = ms[2];
         stats->emit_ms = ms[3];
     }

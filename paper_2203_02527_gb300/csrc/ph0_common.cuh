@@ -194,51 +194,61 @@ struct Layout {
     }
 };
 
-// First homology (k_h1.cu): at most kH1MaxN points (vertex ids packed in
-// 10 bits per triangle), kH1Window triangles reduced per window, kH1Cap
-// entries per column under reduction (the longest measured: 94 at 256
-// uniform points in the plane, 214 at 700, 384 at 1024).  Larger windows
-// measured faster (fewer rounds of the one-CTA ordering step).
-constexpr int64_t kH1MaxN = 1024;
-constexpr int64_t kH1Window = int64_t(1) << 17;
-constexpr int kH1Cap = 512;
-constexpr int kH1ChunkTris = 4096;   // triangles per CTA in the compaction
+// First homology (k_h1.cu): at most kH1MaxN points.  A triangle is named by
+// the 64-bit key (diameter position << 36) | (u << 24) | (v << 12) | w with
+// u < v < w (12 bits per vertex, positions below 2^23 at 4096 points), whose
+// order is the triangle order.  kH1ScanItems: elements per CTA of the
+// prefix scans (1024 threads x 4).
+constexpr int64_t kH1MaxN = 4096;
+constexpr int kH1VertexBits = 12;
+constexpr int kH1Threads = 1024;
+constexpr int64_t kH1ScanItems = 4 * kH1Threads;
 
 // The first-homology regions of a workspace, after the dimension-0 layout.
+// col_cap bounds a column under reduction, pool_cap the reduced columns kept
+// (PH0_ETOOBIG beyond either).
 struct H1Layout {
-    int64_t T, ttiles, W, pool_cap, chunks;
-    size_t thdr, cnt, aof, posof, tkey[2], tval[2], tlook[2], own_tri, own_off, own_len, pair_low, slots,
-        slen, pool, ccount, total;
+    int64_t T, blocks, col_cap, pool_cap;
+    size_t cnt, aof, posof, pmat, tcount, tfirst, scan_in, zpref, tpref, bsum, zlist, rlist, head, claims,
+        node_key, node_pos, node_next, node_within, own_node, own_off, own_len, col_a, col_b, col_m, pool, total;
     H1Layout(int64_t n, size_t base) {
         const int64_t m = n_edges(n);
         T = n * (n - 1) * (n - 2) / 6;
-        ttiles = (T + kSortTile - 1) / kSortTile;
-        W = T < kH1Window ? T : kH1Window;
-        pool_cap = (int64_t(1) << 20) + 16 * m;
-        chunks = (T + kH1ChunkTris - 1) / kH1ChunkTris;
+        blocks = (m + kH1ScanItems - 1) / kH1ScanItems;
+        col_cap = (T < (int64_t(1) << 22) ? T : (int64_t(1) << 22)) + n + 1;
+        pool_cap = (T < (int64_t(1) << 26) ? T : (int64_t(1) << 26)) + n + 1;
         size_t off = base;
         auto take = [&](size_t bytes) {
             size_t o = off;
             off = align_up(off + bytes, 256);
             return o;
         };
-        thdr = take(kHeaderBytes);
+        const size_t M1 = size_t(m + 1);
         cnt = take(256);
-        aof = take(4 * size_t(m + 1));
-        posof = take(4 * size_t(m + 1));
-        for (int b = 0; b < 2; ++b) {
-            tkey[b] = take(8 * size_t(T + 1));
-            tval[b] = take(4 * size_t(T + 1));
-            tlook[b] = take(8 * size_t(ttiles) * kMaxRadix);
-        }
-        own_tri = take(4 * size_t(m + 1));
-        own_off = take(4 * size_t(m + 1));
-        own_len = take(4 * size_t(m + 1));
-        pair_low = take(4 * size_t(T + 1));
-        slots = take(4 * size_t(W) * 2 * kH1Cap);
-        slen = take(4 * size_t(W + 1));
-        pool = take(4 * size_t(pool_cap));
-        ccount = take(4 * size_t(chunks + 1));
+        aof = take(4 * M1);
+        posof = take(4 * M1);
+        pmat = take(4 * size_t(n) * size_t(n));
+        tcount = take(4 * M1);
+        tfirst = take(4 * M1);
+        scan_in = take(8 * M1);
+        zpref = take(8 * M1);
+        tpref = take(8 * M1);
+        bsum = take(8 * size_t(blocks + 1));
+        zlist = take(4 * M1);
+        rlist = take(4 * M1);
+        head = take(4 * M1);
+        claims = take(4 * M1);
+        node_key = take(8 * M1);
+        node_pos = take(4 * M1);
+        node_next = take(4 * M1);
+        node_within = take(4 * M1);
+        own_node = take(4 * M1);
+        own_off = take(8 * M1);
+        own_len = take(4 * M1);
+        col_a = take(8 * size_t(col_cap));
+        col_b = take(8 * size_t(col_cap));
+        col_m = take(16 * size_t(col_cap));
+        pool = take(8 * size_t(pool_cap));
         total = off;
     }
 };

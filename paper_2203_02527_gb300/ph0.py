@@ -170,7 +170,7 @@ def barcodes_profiled(pts: torch.Tensor, ws: Workspace | None = None, bars: torc
 def h1(pts: torch.Tensor):
     """First-homology bars of the Vietoris-Rips 2-skeleton (ph0_h1; waits
     for the GPU): (structured host array in triangle order, stats).  Every
-    positive edge is paired, zero-length bars included; n <= 1024."""
+    positive edge is paired, zero-length bars included; n <= 4096."""
     pts, n, d, ld = _points(pts)
     lib = _lib.load()
     nbytes = int(lib.ph0_h1_workspace_bytes(n, d))
