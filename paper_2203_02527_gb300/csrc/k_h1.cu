@@ -35,11 +35,16 @@
 //      sum of the counts, the rank of every triangle in triangle order;
 //   3. the edges that are the diameter of no triangle, in order: Kruskal
 //      (one thread) marks the spanning-forest edges; the rest are listed;
-//   4. one CTA reduces the listed columns from the latest edge down: a
-//      column is the sorted list of its triangle keys; while its pivot has
-//      an owner (the apparent pair of the pivot's diameter edge, or an
-//      earlier reduced column), the owner's column is added (sorted
-//      symmetric difference); the pivot left is claimed;
+//   4. one CTA reduces the listed columns from the latest edge down: while
+//      a column's pivot has an owner (the apparent pair of the pivot's
+//      diameter edge, or an earlier reduced column), the owner's column is
+//      added; the pivot left is claimed.  A column is a short stack of sorted
+//      runs of triangle keys whose symmetric difference it is: an addition
+//      pushes the owner's column as a run, runs merge (sorted symmetric
+//      difference) while the one below is at most twice as long, and the
+//      pivot is found at the runs' heads, so an addition costs about the
+//      owner's length times the logarithm, not the column's length; the
+//      reduced column is merged into one run and kept;
 //   5. the bars, in triangle order, from the prefix sums of the counts.
 #include "ph0_common.cuh"
 
@@ -337,7 +342,7 @@ struct H1Reduce {
     uint32_t *own_node;        // [m] the claim of each reduced column
     uint64_t *own_off;         // [m] its reduced column in the pool
     uint32_t *own_len;
-    uint64_t *col_a, *col_b, *col_m;
+    uint64_t *col_x, *col_m;
     int64_t col_cap;
     uint64_t *pool;
     int64_t pool_cap;
@@ -422,17 +427,112 @@ __device__ int64_t h1_symdiff(const uint64_t *A, int64_t LA, const uint64_t *B, 
     return int64_t(kept);
 }
 
+// The column under reduction: up to kH1Runs sorted runs of keys in X,
+// stacked in allocation order; the column is the symmetric difference of
+// their live parts [head, end) (heads advance over keys that cancel in
+// pairs).  Kept in shared memory, changed by thread 0 between barriers.
+struct H1Runs {
+    int64_t off[kH1Runs], head[kH1Runs], end[kH1Runs];
+    int64_t top;  // first free key of X
+    int nr;
+};
+
+// Merge the top two runs into the lower one's place (all threads).  The
+// result is no longer than the two, and h1_symdiff reads its inputs only
+// before its first barrier, so it may overwrite them.
+__device__ void h1_merge_top(H1Runs &S, uint64_t *X, uint64_t *M, uint64_t *s_warp) {
+    const int i = S.nr - 2;
+    const int64_t la = S.end[i] - S.head[i], lb = S.end[i + 1] - S.head[i + 1];
+    const int64_t lc = h1_symdiff(X + S.head[i], la, X + S.head[i + 1], lb, M, X + S.off[i], la + lb, s_warp);
+    if (threadIdx.x == 0) {
+        S.head[i] = S.off[i];
+        S.end[i] = S.off[i] + lc;
+        S.top = S.end[i];
+        S.nr = i + 1;
+    }
+    __syncthreads();
+}
+
+// Push src[0, len) as a new run (all threads), merging runs while the one
+// below is at most twice as long (so lengths fall geometrically up the
+// stack); when X or the run table is full, every run is merged first and the
+// one left moved to the bottom.  False if it still does not fit.
+__device__ bool h1_push(H1Runs &S, uint64_t *X, int64_t cap, uint64_t *M, const uint64_t *src, int64_t len,
+                        uint64_t *s_warp) {
+    if (S.nr == kH1Runs || S.top + len > cap) {
+        while (S.nr >= 2) h1_merge_top(S, X, M, s_warp);
+        if (S.nr == 1 && S.head[0] > S.off[0]) {
+            const int64_t h = S.head[0], l = S.end[0] - S.head[0];
+            for (int64_t i = threadIdx.x; i < l; i += blockDim.x) M[i] = X[h + i];
+            __syncthreads();
+            for (int64_t i = threadIdx.x; i < l; i += blockDim.x) X[i] = M[i];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.off[0] = 0;
+                S.head[0] = 0;
+                S.end[0] = l;
+                S.top = l;
+            }
+            __syncthreads();
+        }
+    }
+    if (S.top + len > cap) return false;
+    const int64_t o = S.top;
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) X[o + i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S.off[S.nr] = o;
+        S.head[S.nr] = o;
+        S.end[S.nr] = o + len;
+        S.top = o + len;
+        S.nr += 1;
+    }
+    __syncthreads();
+    while (S.nr >= 2 && S.end[S.nr - 2] - S.head[S.nr - 2] <= 2 * (S.end[S.nr - 1] - S.head[S.nr - 1]))
+        h1_merge_top(S, X, M, s_warp);
+    return true;
+}
+
+// The pivot of the column (thread 0): the smallest key at the heads of the
+// runs held by an odd number of them; keys held by an even number cancel and
+// their heads advance.  False for an empty column.
+__device__ bool h1_pivot(H1Runs &S, const uint64_t *X, uint64_t &piv) {
+    for (;;) {
+        uint64_t mn = ~0ull;
+        int c = 0;
+        for (int r = 0; r < S.nr; ++r) {
+            if (S.head[r] >= S.end[r]) continue;
+            const uint64_t k = X[S.head[r]];
+            if (k < mn) {
+                mn = k;
+                c = 1;
+            } else if (k == mn) {
+                ++c;
+            }
+        }
+        if (c == 0) return false;
+        if (c & 1) {
+            piv = mn;
+            return true;
+        }
+        for (int r = 0; r < S.nr; ++r)
+            if (S.head[r] < S.end[r] && X[S.head[r]] == mn) S.head[r] += 1;
+    }
+}
+
 // One CTA: the listed columns from the latest edge down (see the top).
 __global__ void __launch_bounds__(kH1Threads) k_h1_reduce(H1Reduce R) {
     __shared__ uint64_t s_keys[kH1MaxN];
     __shared__ uint64_t s_warp[kH1Threads / 32 + 1];
+    __shared__ H1Runs S;
+    __shared__ uint64_t s_piv;
     __shared__ int32_t s_owner, s_app, s_err;
     __shared__ uint32_t s_node;
     const uint32_t *vals = (make_plan(R.esort).passes & 1) ? R.vals1 : R.vals0;
     const int tid = threadIdx.x;
     const int64_t n = R.n;
     const int64_t K = int64_t(R.c->reduced);
-    uint64_t *A = R.col_a, *C = R.col_b;
+    uint64_t *X = R.col_x, *M = R.col_m;
     unsigned long long adds = 0, maxlen = 0, pool_used = 0, nodes = 0;
     if (tid == 0) s_err = 0;
     __syncthreads();
@@ -440,34 +540,37 @@ __global__ void __launch_bounds__(kH1Threads) k_h1_reduce(H1Reduce R) {
         const uint32_t p = R.rlist[k];
         uint32_t a, b;
         h1_uv(vals, p, n, a, b);  // listed from checked records
-        h1_cobound(R.P, n, a, b, p, s_keys);
-        int64_t LA = n - 2;
-        for (int64_t i = tid; i < LA; i += blockDim.x) A[i] = s_keys[i];
+        if (tid == 0) {
+            S.nr = 0;
+            S.top = 0;
+        }
         __syncthreads();
-        uint64_t piv = 0;
+        h1_cobound(R.P, n, a, b, p, s_keys);
+        h1_push(S, X, R.col_cap, M, s_keys, n - 2, s_warp);  // fits: col_cap > n
         for (;;) {
-            if (LA == 0) {  // every positive column keeps a pivot: a bug if not
-                if (tid == 0) s_err = PH0_EINTERNAL;
-                break;
-            }
-            piv = A[0];
             if (tid == 0) {
-                const uint32_t dp = h1_key_dpos(piv);
-                uint32_t a2, b2;
-                if (!h1_uv(vals, dp, n, a2, b2)) s_err = PH0_EINTERNAL;
-                if (adds >= kH1MaxAdditions) s_err = PH0_ETOOBIG;
                 int32_t owner = -1, app = 0;
-                const int32_t f = R.tfirst[dp];
-                if (f >= 0 && h1_key(dp, a2, b2, uint32_t(f)) == piv) {
-                    owner = int32_t(dp);
-                    app = 1;
+                uint64_t piv = 0;
+                if (!h1_pivot(S, X, piv)) {
+                    s_err = PH0_EINTERNAL;  // every positive column keeps a pivot: a bug if not
                 } else {
-                    for (int32_t q = R.head[dp]; q >= 0; q = R.node_next[q])
-                        if (R.node_key[q] == piv) {
-                            owner = int32_t(R.node_pos[q]);
-                            break;
-                        }
+                    const uint32_t dp = h1_key_dpos(piv);
+                    uint32_t a2, b2;
+                    if (!h1_uv(vals, dp, n, a2, b2)) s_err = PH0_EINTERNAL;
+                    if (adds >= kH1MaxAdditions) s_err = PH0_ETOOBIG;
+                    const int32_t f = R.tfirst[dp];
+                    if (f >= 0 && h1_key(dp, a2, b2, uint32_t(f)) == piv) {
+                        owner = int32_t(dp);
+                        app = 1;
+                    } else {
+                        for (int32_t q = R.head[dp]; q >= 0; q = R.node_next[q])
+                            if (R.node_key[q] == piv) {
+                                owner = int32_t(R.node_pos[q]);
+                                break;
+                            }
+                    }
                 }
+                s_piv = piv;
                 s_owner = owner;
                 s_app = app;
             }
@@ -477,34 +580,26 @@ __global__ void __launch_bounds__(kH1Threads) k_h1_reduce(H1Reduce R) {
             const bool stop = s_err != 0;
             __syncthreads();
             if (stop || owner < 0) break;
-            const uint64_t *B;
-            int64_t LB;
+            bool ok;
             if (app) {
                 uint32_t a2, b2;
                 h1_uv(vals, owner, n, a2, b2);  // checked above as the pivot's diameter edge
                 h1_cobound(R.P, n, a2, b2, uint32_t(owner), s_keys);
-                B = s_keys;
-                LB = n - 2;
+                ok = h1_push(S, X, R.col_cap, M, s_keys, n - 2, s_warp);
             } else {
-                B = R.pool + R.own_off[owner];
-                LB = R.own_len[owner];
+                ok = h1_push(S, X, R.col_cap, M, R.pool + R.own_off[owner], R.own_len[owner], s_warp);
             }
-            const int64_t LC = h1_symdiff(A, LA, B, LB, R.col_m, C, R.col_cap, s_warp);
-            if (LC < 0) {
+            if (!ok) {
                 if (tid == 0) s_err = PH0_ETOOBIG;
                 __syncthreads();
                 break;
             }
-            uint64_t *t = A;
-            A = C;
-            C = t;
-            LA = LC;
             ++adds;
-            if (uint64_t(LA) > maxlen) maxlen = uint64_t(LA);
         }
         __syncthreads();
         if (s_err) break;
         // claim the pivot: a node in the list of its diameter position
+        const uint64_t piv = s_piv;
         const uint32_t dp = h1_key_dpos(piv);
         uint32_t a2, b2, u, v, w;
         h1_uv(vals, dp, n, a2, b2);  // checked above
@@ -527,18 +622,22 @@ __global__ void __launch_bounds__(kH1Threads) k_h1_reduce(H1Reduce R) {
         uint64_t within;
         h1_block_scan(cnt, s_warp, within);
         if (tid == 0) R.node_within[s_node] = uint32_t(within);
-        // keep the reduced column for the columns below
+        // the reduced column, one sorted run (its first key is the pivot),
+        // kept for the columns below
+        while (S.nr >= 2) h1_merge_top(S, X, M, s_warp);
+        const int64_t h0 = S.head[0], LA = S.end[0] - S.head[0];
         if (int64_t(pool_used) + LA > R.pool_cap) {
             if (tid == 0) s_err = PH0_ETOOBIG;
             __syncthreads();
             break;
         }
-        for (int64_t i = tid; i < LA; i += blockDim.x) R.pool[pool_used + i] = A[i];
+        for (int64_t i = tid; i < LA; i += blockDim.x) R.pool[pool_used + i] = X[h0 + i];
         if (tid == 0) {
             R.own_off[p] = pool_used;
             R.own_len[p] = uint32_t(LA);
         }
         pool_used += uint64_t(LA);
+        if (uint64_t(LA) > maxlen) maxlen = uint64_t(LA);
         __syncthreads();
     }
     if (tid == 0) {
@@ -672,8 +771,7 @@ cudaError_t run_h1(void *ws, const H1Layout &H, int64_t n, const uint64_t *ek0, 
     R.own_node = at<uint32_t>(ws, H.own_node);
     R.own_off = at<uint64_t>(ws, H.own_off);
     R.own_len = at<uint32_t>(ws, H.own_len);
-    R.col_a = at<uint64_t>(ws, H.col_a);
-    R.col_b = at<uint64_t>(ws, H.col_b);
+    R.col_x = at<uint64_t>(ws, H.col_x);
     R.col_m = at<uint64_t>(ws, H.col_m);
     R.col_cap = H.col_cap;
     R.pool = at<uint64_t>(ws, H.pool);

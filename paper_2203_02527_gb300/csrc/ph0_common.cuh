@@ -198,24 +198,27 @@ struct Layout {
 // the 64-bit key (diameter position << 36) | (u << 24) | (v << 12) | w with
 // u < v < w (12 bits per vertex, positions below 2^23 at 4096 points), whose
 // order is the triangle order.  kH1ScanItems: elements per CTA of the
-// prefix scans (1024 threads x 4).
+// prefix scans (1024 threads x 4); kH1Runs: sorted runs of a column under
+// reduction.
 constexpr int64_t kH1MaxN = 4096;
 constexpr int kH1VertexBits = 12;
 constexpr int kH1Threads = 1024;
 constexpr int64_t kH1ScanItems = 4 * kH1Threads;
+constexpr int kH1Runs = 32;
 
 // The first-homology regions of a workspace, after the dimension-0 layout.
 // col_cap bounds a column under reduction, pool_cap the reduced columns kept
-// (PH0_ETOOBIG beyond either).
+// (PH0_ETOOBIG beyond either): the runs of a column live in col_x, col_m
+// holds a merge.
 struct H1Layout {
     int64_t T, blocks, col_cap, pool_cap;
     size_t cnt, aof, posof, pmat, tcount, tfirst, scan_in, zpref, tpref, bsum, zlist, rlist, head, claims,
-        node_key, node_pos, node_next, node_within, own_node, own_off, own_len, col_a, col_b, col_m, pool, total;
+        node_key, node_pos, node_next, node_within, own_node, own_off, own_len, col_x, col_m, pool, total;
     H1Layout(int64_t n, size_t base) {
         const int64_t m = n_edges(n);
         T = n * (n - 1) * (n - 2) / 6;
         blocks = (m + kH1ScanItems - 1) / kH1ScanItems;
-        col_cap = (T < (int64_t(1) << 22) ? T : (int64_t(1) << 22)) + n + 1;
+        col_cap = (T < (int64_t(1) << 23) ? T : (int64_t(1) << 23)) + 2 * n + 1;
         pool_cap = (T < (int64_t(1) << 26) ? T : (int64_t(1) << 26)) + n + 1;
         size_t off = base;
         auto take = [&](size_t bytes) {
@@ -245,9 +248,8 @@ struct H1Layout {
         own_node = take(4 * M1);
         own_off = take(8 * M1);
         own_len = take(4 * M1);
-        col_a = take(8 * size_t(col_cap));
-        col_b = take(8 * size_t(col_cap));
-        col_m = take(16 * size_t(col_cap));
+        col_x = take(8 * size_t(col_cap));
+        col_m = take(8 * size_t(col_cap));
         pool = take(8 * size_t(pool_cap));
         total = off;
     }
