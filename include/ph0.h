@@ -278,7 +278,8 @@ int ph0_reduce(int64_t n, const uint32_t *val_sorted_dev,
  *
  * Synchronous: it waits for `stream` and reads the device status back
  * before returning (as ph0_finish() would), so it cannot be recorded into a
- * CUDA graph.  The first call on a device looks up the device address of the
+ * CUDA graph: on a stream under capture it returns PH0_EINVAL before
+ * anything is queued, and the caller's capture stays valid.  The first call on a device looks up the device address of the
  * array for that device (with that device current) and keeps it for the rest
  * of the process; after a cudaDeviceReset() of that device the kept address
  * is stale, so this entry point must not be called again in that process.

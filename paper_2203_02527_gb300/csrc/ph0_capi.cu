@@ -753,6 +753,11 @@ extern "C" int ph0_barcodes_noalloc(const float *pts_dev, int64_t n, int32_t d, 
     if (!aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8)) return PH0_EINVAL;
     const Layout L(n, d);
     if (L.total > kNoAllocScratchBytes) return PH0_ETOOBIG;
+    {  // it waits for its stream, which a capture forbids: refuse before queueing anything
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) return PH0_ECUDA;
+        if (cs != cudaStreamCaptureStatusNone) return PH0_EINVAL;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PH0_ECUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return PH0_EINVAL;

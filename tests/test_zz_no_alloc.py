@@ -114,3 +114,27 @@ def test_noalloc_rejects_clouds_beyond_its_array():
     pts = torch.zeros((n, d), device="cuda")
     bars = torch.empty((n - 1, 40), dtype=torch.uint8, device="cuda")
     assert lib.ph0_barcodes_noalloc(vp(pts.data_ptr()), n, d, d, vp(bars.data_ptr()), None, None) == 3
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    """The call waits for its stream, which a capture forbids: on a stream
+    being captured it returns PH0_EINVAL at once and queues nothing, so the
+    caller's capture ends normally and replays; then the same call outside the
+    capture gives the oracle's bars."""
+    lib = _lib().load()
+    x = inputs.uniform(200, 3, seed=77)
+    pts = torch.from_numpy(x).cuda()
+    bars = torch.empty((199, 40), dtype=torch.uint8, device="cuda")
+    src = torch.arange(1024, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        rc = lib.ph0_barcodes_noalloc(vp(pts.data_ptr()), 200, 3, 3, vp(bars.data_ptr()), None,
+                                      vp(s.cuda_stream))
+        out = src * 2
+    assert rc == 1  # PH0_EINVAL
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, src * 2)
+    np.testing.assert_array_equal(_bars_noalloc(lib, pts), _oracle_raw(x))
