@@ -39,7 +39,7 @@ WORKLOAD = "circles32768"
 # (profiles/kernels_circles8192.md), scaled by edges to the benchmark cloud:
 # the distance kernel, one radix pass (mean of the captured slots 4, 5 and
 # the top pass), the fix-up.
-PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 25.28, "k_sort_fixup": 8.18}
+PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 25.31, "k_sort_fixup": 8.18}
 ONESWEEP_TRAFFIC_PER_EDGE = PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
 # the algorithmic floor of the phase (steps 1-3): write the records (12 B),
 # read and write them once to sort (24 B), read the keys and write a (12 B)
