@@ -215,6 +215,13 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
  * with `ws` and, when stats != NULL, its counters. */
 int ph0_finish(const void *ws, void *stream, ph0_stats *stats);
 
+/* Byte offset, within a workspace, of the int32 ph0_status of the last
+ * call's device-side work (the word ph0_finish() reads; the same for every n
+ * and d).  A caller that must not wait between calls, such as one replaying
+ * a CUDA graph of many calls, can copy these words from all its workspaces
+ * at once and check them afterwards.  No counterpart in the paper. */
+size_t ph0_status_offset(void);
+
 /* Tracing aid: copies to `out` (host, max_windows x 12 uint64) the per-window
  * records of the last reduction run on `ws` for a cloud of (n, d):
  * {first position, window size, candidates, grid-wide rounds, shared-memory

@@ -144,6 +144,7 @@ SIGNATURES = {
     "ph0_barcodes_early_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
                                                 ctypes.POINTER(Tuning), ctypes.POINTER(Stats)]),
     "ph0_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Stats)]),
+    "ph0_status_offset": (ctypes.c_size_t, []),
     "ph0_barcodes_tuned": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,
                                           ctypes.POINTER(Tuning)]),
     "ph0_barcodes_profiled": (ctypes.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP, _SZ, _VP,

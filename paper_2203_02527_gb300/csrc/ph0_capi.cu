@@ -288,6 +288,11 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     return cuda_status(e);
 }
 
+size_t ph0_status_offset(void) {
+    static_assert(offsetof(Header, status) == 0, "the status word leads the header");
+    return Layout(2, 1).hdr + offsetof(Header, status);  // the header is the first region for every size
+}
+
 int ph0_barcodes(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                  ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream) {
     return ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);

@@ -306,7 +306,9 @@ def death_values(pts: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor
 class DeathValuesBatch(torch.autograd.Function):
     """DeathValues over many clouds at once: every cloud's forward path and
     backward kernel is queued on one of several CUDA streams, so the clouds'
-    kernels overlap on the GPU; the statuses are read once all are queued."""
+    kernels overlap on the GPU; the statuses are read once all are queued.
+    While the current stream is being captured into a CUDA graph nothing
+    waits: the statuses are left to Batch.check() after each replay."""
 
     @staticmethod
     def forward(ctx, workspaces, streams, *pts):
@@ -317,9 +319,10 @@ class DeathValuesBatch(torch.autograd.Function):
             s.wait_stream(cur)
             with torch.cuda.stream(s):
                 bars.append(barcodes(p, workspaces[i], sync=False))
-        for i, ws in enumerate(workspaces[:len(pts)]):
-            with torch.cuda.stream(streams[i % len(streams)]):
-                finish(ws)  # waits for that stream; raises on a device error
+        if not torch.cuda.is_current_stream_capturing():
+            for i, ws in enumerate(workspaces[:len(pts)]):
+                with torch.cuda.stream(streams[i % len(streams)]):
+                    finish(ws)  # waits for that stream; raises on a device error
         for s in streams:
             cur.wait_stream(s)
         out = [b.death for b in bars]  # on the current stream, after every cloud finished
@@ -357,3 +360,18 @@ class Batch:
         """Finite death values of every cloud (a tuple of float64 tensors),
         differentiable with respect to each cloud's points."""
         return DeathValuesBatch.apply(self.workspaces, self.streams, *pts_list)
+
+    def check(self):
+        """Raise on a device error of the last calls on these workspaces
+        (after replaying a captured step): every status word in one copy."""
+        for i, st in enumerate(statuses(self.workspaces)):
+            if st != 0:
+                raise _lib.Ph0Error(int(st), f"cloud {i}")
+
+
+def statuses(workspaces) -> list:
+    """The ph0_status of the last call on each workspace (one device copy,
+    then a wait for the current stream)."""
+    off = int(_lib.load().ph0_status_offset())
+    words = torch.stack([w.buf[off:off + 4] for w in workspaces]).view(torch.int32)
+    return words.flatten().tolist()

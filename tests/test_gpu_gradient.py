@@ -114,3 +114,55 @@ def test_batched_death_values_equal_one_at_a_time():
         assert torch.equal(one, dv)
         (one ** 2).sum().backward()
         np.testing.assert_allclose(p.grad.cpu().numpy(), q.grad.cpu().numpy(), rtol=1e-6, atol=1e-9)
+
+
+def test_captured_batched_step_replays_the_eager_steps():
+    """The batched descent step captured once into a CUDA graph and replayed
+    follows the eager trajectory: the same deaths at every step (the pairing
+    and distances are exact), the points within the last bit of the binary64
+    gradient sums (accumulated by atomics in any order), and the statuses of
+    every cloud read in one copy after each replay."""
+    ph0 = _ph0()
+    xs = [inputs.uniform(600 + 50 * c, 3, seed=3000 + c) for c in range(10)]
+
+    def trajectory(graphed):
+        pts = [torch.from_numpy(x).cuda().requires_grad_(True) for x in xs]
+        opt = torch.optim.SGD(pts, lr=1e-2)
+        batch = ph0.Batch([x.shape for x in xs], streams=4)
+        losses = []
+
+        def step():
+            deaths = batch.death_values(pts)
+            total = sum((dv ** 2).sum() for dv in deaths)
+            total.backward()
+            opt.step()
+            return total
+
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                opt.zero_grad(set_to_none=True)
+                losses.append(float(step().detach()))
+        torch.cuda.current_stream().wait_stream(side)
+        if graphed:
+            graph = torch.cuda.CUDAGraph()
+            opt.zero_grad(set_to_none=True)
+            with torch.cuda.graph(graph):
+                static_total = step()
+            for _ in range(5):
+                graph.replay()
+                losses.append(float(static_total.detach()))
+                batch.check()
+        else:
+            for _ in range(5):
+                opt.zero_grad(set_to_none=True)
+                losses.append(float(step().detach()))
+        return losses, [p.detach().cpu().numpy() for p in pts]
+
+    l_eager, p_eager = trajectory(False)
+    l_graph, p_graph = trajectory(True)
+    np.testing.assert_allclose(l_graph, l_eager, rtol=1e-9)
+    for a, b in zip(p_graph, p_eager):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-6)
+    assert l_graph[-1] < l_graph[0]
