@@ -141,15 +141,17 @@ cudaError_t sort_fallback(void *ws, const Layout &L, const float *pts, int64_t n
 // then a fix-up of the groups they leave, which also counts the new
 // distance values of every de-duplication chunk into cpref; k_sort.cu) and
 // its gated fallback.  The sorted records end in buffer (passes & 1) of h's
-// plan; step 3 then needs only launch_dedupe_scan.
+// plan; step 3 then needs only launch_dedupe_scan.  fallback = false leaves
+// the fallback out: the result is then exact only when h->fixup_fallback
+// stays 0 (a caller that waits for the call checks it and runs again).
 cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, int32_t d, int64_t ld,
-                       const Tune &t, cudaStream_t s) {
+                       const Tune &t, cudaStream_t s, bool fallback = true) {
     if (L.m <= 0) return cudaSuccess;
     cudaError_t e = launch_sort_short(at<uint64_t>(ws, L.key[0]), at<uint64_t>(ws, L.key[1]),
                                       at<uint32_t>(ws, L.val[0]), at<uint32_t>(ws, L.val[1]), L.m,
                                       at<uint64_t>(ws, L.look[0]), at<uint64_t>(ws, L.look[1]),
                                       at<Header>(ws, L.hdr), at<uint32_t>(ws, L.cpref), s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !fallback) return e;
     return sort_fallback(ws, L, pts, n, d, ld, t, s);
 }
 
@@ -234,6 +236,10 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
 }
 
 }  // namespace
+int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                   ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning,
+                   bool fallback);
+
 }  // namespace ph0
 
 using namespace ph0;
@@ -265,6 +271,17 @@ size_t ph0_workspace_bytes(int64_t n, int32_t d) {
 int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                        ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream,
                        const ph0_tuning *tuning) {
+    return ph0::barcodes_whole(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, tuning, true);
+}
+}  // extern "C"
+
+namespace ph0 {
+// The whole path (ph0_barcodes_tuned); fallback = false leaves out the
+// gated complete sort (see sort_whole): for a caller that waits for the call
+// and reads h->fixup_fallback (the serving context).
+int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                   ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning,
+                   bool fallback) {
     int rc = check_sizes(n, d, ld, kMaxNWide);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
@@ -280,13 +297,16 @@ int ph0_barcodes_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t ld, p
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
-    if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s);
+    if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s, fallback);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, nullptr,
                             t.spin_limit, t.wide);
     return cuda_status(e);
 }
+}  // namespace ph0
+
+extern "C" {
 
 size_t ph0_status_offset(void) {
     static_assert(offsetof(Header, status) == 0, "the status word leads the header");

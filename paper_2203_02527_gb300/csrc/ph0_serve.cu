@@ -37,6 +37,9 @@ cudaError_t launch_small(const SmallTask *tasks, const int32_t *ntasks_dev, uint
 int small_max_n();
 int small_max_d();
 int sm_count();
+int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
+                   ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning,
+                   bool fallback);
 
 namespace {
 
@@ -89,7 +92,8 @@ struct Request {
     int32_t status = PH0_OK;
     int32_t inf_vertex = 0;
     bool small = false;
-    // pinned host: [points | bars | status word]
+    bool full = false;  // run with the complete sort's fallback (after its flag was seen)
+    // pinned host: [points | bars | status words: status, infinite bar's vertex, fallback flag]
     size_t h_off = 0, h_bytes = 0;
     // device: [points | bars | workspace or fixed-point scratch | status]
     size_t d_off = 0, d_bytes = 0;
@@ -169,7 +173,11 @@ struct ph0_ctx {
         finished.push_back(r);
     }
 
-    // Launch one large request on stream slot `k`.
+    // Launch one large request on stream slot `k`.  The first launch leaves
+    // out the whole path's gated fallback (about 14 launches that return at
+    // once on almost every cloud) and copies the fix-up's fallback flag back
+    // with the status; a request whose flag is set runs again in full
+    // before it completes, so every result is still exact.
     cudaError_t launch_large(Request *r, int k) {
         cudaStream_t s = streams[k];
         char *base = dev + r->d_off;
@@ -179,13 +187,17 @@ struct ph0_ctx {
                    align_up(size_t(r->n > 1 ? r->n - 1 : 1) * sizeof(ph0_bar), 256);
         cudaError_t e = cudaMemcpyAsync(d_pts, pts_host(r), size_t(r->n) * r->d * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return e;
-        const int rc = ph0_barcodes(d_pts, r->n, r->d, r->d, d_bars, nullptr, ws, r->ws_bytes, s);
+        const int rc = barcodes_whole(d_pts, r->n, r->d, r->d, d_bars, nullptr, ws, r->ws_bytes, s, nullptr, r->full);
         if (rc != PH0_OK) return cudaErrorUnknown;
         if (r->n > 1)
             e = cudaMemcpyAsync(bars_host(r), d_bars, size_t(r->n - 1) * sizeof(ph0_bar), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(status_host(r), ws, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                 s);  // header: status, vertex of the infinite bar
+        status_host(r)[2] = 0;
+        if (e == cudaSuccess && !r->full)
+            e = cudaMemcpyAsync(status_host(r) + 2, &at<Header>(ws, Layout(r->n, r->d).hdr)->fixup_fallback,
+                                sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(events[k], s);
         return e;
     }
@@ -239,8 +251,17 @@ struct ph0_ctx {
                 busy = true;
                 const cudaError_t q = cudaEventQuery(events[k]);
                 if (q == cudaErrorNotReady) continue;
-                if (q == cudaSuccess) complete_ok(r);
-                else complete(r, PH0_ECUDA);
+                if (q == cudaSuccess && !r->full && status_host(r)[0] == PH0_OK && status_host(r)[2] != 0) {
+                    r->full = true;  // crowded distances: the complete sort, on the same slot
+                    const cudaError_t e = launch_large(r, int(k));
+                    if (e == cudaSuccess) continue;
+                    error = e;
+                    complete(r, PH0_ECUDA);
+                } else if (q == cudaSuccess) {
+                    complete_ok(r);
+                } else {
+                    complete(r, PH0_ECUDA);
+                }
                 slot_req[k] = nullptr;
                 cv_done.notify_all();
             }

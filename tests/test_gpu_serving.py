@@ -74,6 +74,37 @@ def test_mixed_stream_equals_plain_under_tight_budget():
         _same(done[i].bars, _plain(x))
 
 
+def _crowded(n, seed):
+    # two clusters within 1e-12 of two points at distance 1: the cross
+    # distances crowd into one long group of equal key >> 16 out of order, so
+    # the fix-up asks for the complete sort
+    rng = np.random.default_rng(seed)
+    a = rng.random((n // 2, 3)) * 1e-12
+    b = rng.random((n - n // 2, 3)) * 1e-12
+    b[:, 1] = 1.0
+    return np.ascontiguousarray(np.concatenate([a, b]), np.float32)
+
+
+def test_served_crowded_clouds_run_again_with_the_complete_sort():
+    """The serving context leaves the whole path's gated complete sort out and
+    runs a cloud again in full when the fix-up flags it: clouds that need it,
+    mixed with clouds that do not, still give exactly the plain path's bars
+    (and the oracle's)."""
+    from paper_2203_02527_gb300.serve import Server, run_stream
+    clouds = []
+    for i in range(24):
+        clouds.append(_crowded(300 + 37 * i, seed=900 + i) if i % 2 == 0
+                      else inputs.gaussian_mixture(250 + 41 * i, 3, k=3, sigma=0.3, seed=950 + i))
+    with Server(mem_budget=4 << 30, streams=4, small_max_n=180, batch_max=32) as srv:
+        done = run_stream(srv, clouds)
+    for i, x in enumerate(clouds):
+        assert done[i].status == 0
+        _same(done[i].bars, _plain(x))
+        if i % 6 == 0:
+            want = oracle.barcodes(x)[0]
+            assert done[i].bars.tobytes() == want.astype(done[i].bars.dtype).tobytes()
+
+
 def test_serving_errors():
     from paper_2203_02527_gb300._lib import Ph0Error
     from paper_2203_02527_gb300.serve import Server
