@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     const int64_t gstride = G * kReduceThreads;
     const uint32_t target = uint32_t(n - 1);
 
-    int64_t pos0 = 0, W = A.w0;
+    int64_t pos0 = A.start, W = A.w0;
     uint32_t round = 0;       // grid rounds: identical in every CTA (claim tags)
     int64_t tail_total = 0;   // shared-memory rounds (CTA 0)
     int windows = 0;
@@ -511,11 +511,12 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     }
     claims = __reduce_add_sync(0xffffffffu, claims);
     if ((tid & 31) == 0 && claims) atomicAdd(&h->claim_attempts, (unsigned long long)claims);
-    if (blockIdx.x == 0 && tid == 0) {
-        h->windows = windows;
+    if (blockIdx.x == 0 && tid == 0) {  // a resumed launch adds to the earlier ones
+        const bool add = A.start > 0;
+        h->windows = (add ? h->windows : 0) + windows;
         h->edges_scanned = pos0;
-        h->candidates = candidates;
-        h->rounds = int64_t(round) + tail_total;
+        h->candidates = (add ? h->candidates : 0) + candidates;
+        h->rounds = (add ? h->rounds : 0) + int64_t(round) + tail_total;
         h->n_bars = __ldcg(&h->npiv);
         atomicMax(&h->claim_rounds_max, rounds_max);
     }
@@ -617,9 +618,11 @@ cudaError_t launch_reduce(const ReduceArgs &A, cudaStream_t s) {
     int blocks = int((A.n + 255) / 256);
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
-    k_reduce_init<<<blocks, 256, 0, s>>>(A);
+    // a launch that resumes (start > 0) keeps the roots, claims and pivots of
+    // the earlier one: it ended at a window boundary, the end of its edges
+    if (A.start == 0) k_reduce_init<<<blocks, 256, 0, s>>>(A);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || A.m <= 0) return e;
+    if (e != cudaSuccess || A.m <= A.start) return e;
 
     const size_t smem = reduce_dyn_smem(A.n, A.wide);
     const void *fn = A.wide ? (const void *)k_reduce<true> : (const void *)k_reduce<false>;

@@ -160,7 +160,7 @@ cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, i
 // selects the one holding the sorted data) or the caller's.
 cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                        const uint32_t *val1, const Header *sort_h, cudaStream_t s,
-                       uint32_t spin_limit = kSpinLimit, bool wide = false) {
+                       uint32_t spin_limit = kSpinLimit, bool wide = false, int64_t start = 0) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -183,6 +183,7 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
     int64_t w0 = 2 * n > 4096 ? 2 * n : 4096;
     A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
     A.spin_limit = spin_limit;
+    A.start = start;
     return launch_reduce(A, s);
 }
 
@@ -420,8 +421,19 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
     int64_t P = 0;
     bool done = false;
     for (int c = 0; c < nc && !done; ++c) {
-        const int64_t c0 = cstart[c], seg = cstart[c + 1] - c0;
-        if (seg == 0) continue;
+        if (cstart[c + 1] == cstart[c]) continue;
+        // the segment starts at the class start rounded down to 4 records, so
+        // that its rows stay 16-byte aligned (bulk tile loads in every pass):
+        // the at most 3 records before the class, already sorted into buffer
+        // 0 with keys below every key of the class, are copied ahead of it in
+        // buffer 1 and sort to where they are
+        const int64_t c0 = cstart[c] & ~int64_t(3), seg = cstart[c + 1] - c0, lead = cstart[c] - c0;
+        if (lead > 0) {
+            e = cudaMemcpyAsync(k1 + c0, k0 + c0, size_t(lead) * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(v1 + c0, v0 + c0, size_t(lead) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return PH0_ECUDA;
+        }
         const int64_t stiles = (seg + kSortTile - 1) / kSortTile;
         uint64_t *sk0 = k1 + c0, *sk1 = k0 + c0;  // the segment's buffers 0 and 1
         uint32_t *sv0 = v1 + c0, *sv1 = v0 + c0;
@@ -449,9 +461,11 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
         if (e == cudaSuccess) e = launch_sort_passes(sk0, sk1, sv0, sv1, seg, look0, look1, sh, s, true);
         if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, seg, sh, 0, fb, s);
         if (e != cudaSuccess) return PH0_ECUDA;
+        const int64_t Pprev = P;
         P = c0 + seg;
-        // steps 4-5 on the prefix; enough once it holds n-1 pivots
-        e = run_reduce(ws, L, n, P, v0, v0, nullptr, s);
+        // steps 4-5 on the prefix, resumed where the last round stopped;
+        // enough once it holds n-1 pivots
+        e = run_reduce(ws, L, n, P, v0, v0, nullptr, s, kSpinLimit, false, Pprev);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         Header hh;
         if (e == cudaSuccess) e = cudaMemcpy(&hh, h, sizeof(Header), cudaMemcpyDeviceToHost);

@@ -276,6 +276,8 @@ struct ReduceArgs {
     uint32_t *kill_val;            // [n] its pivot row
     Header *h;
     int64_t w0;                    // first window size
+    int64_t start;                 // first position to scan: 0, or where an earlier launch on the
+                                   // same workspace stopped (its state carried, no re-initialization)
     uint64_t *trace;               // [kTraceWindows][kTraceWords]
     uint32_t spin_limit;           // polls before a grid-barrier wait gives up
 };
