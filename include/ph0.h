@@ -38,10 +38,15 @@
  * device-detected errors (non-finite input, a bounded wait that timed out) in
  * the workspace, where ph0_finish() reads them.
  *
- * Limits: 1 <= N <= 92681 (E = N(N-1)/2 < 2^32, so every position, count
- * and index a is a 32-bit number; the N = 92681 workspace is about 113 GB)
- * for the whole-path entry points, 1 <= N <= 65535 for the step entry points
- * (whose edge records pack (u << 16) | v), 1 <= d <= 1024.
+ * Limits: 1 <= N <= 131071 for ph0_barcodes(), ph0_barcodes_tuned() and
+ * ph0_workspace_bytes() (E = N(N-1)/2 < 2^33 edges: above 92,682 points the
+ * records carry bit 32 of the edge index in the key's sign bit, the sort takes
+ * two halves of fewer than 2^32 edges and merges them, and the reduction scans
+ * at most the first 2^32 - 4096 sorted edges, enough for the n-1 killing edges
+ * of any cloud whose last merge comes before that position: PH0_ETOOBIG
+ * otherwise; the N = 100,000 workspace is about 132 GB), 1 <= N <= 92681 for
+ * the other whole-path entry points (E < 2^32), 1 <= N <= 65535 for the step
+ * entry points (whose edge records pack (u << 16) | v), 1 <= d <= 1024.
  */
 #ifndef PH0_H
 #define PH0_H
@@ -57,7 +62,7 @@ typedef enum {
     PH0_OK = 0,
     PH0_EINVAL = 1,      /* bad argument: n < 1, d < 1, ld < d, null or misaligned pointer */
     PH0_ENONFINITE = 2,  /* a coordinate is NaN or +-Inf (detected on the device) */
-    PH0_ETOOBIG = 3,     /* n > 92681 (65535 for the step entry points) or d > 1024 */
+    PH0_ETOOBIG = 3,     /* n above the entry point's limit (see Limits) or d > 1024 */
     PH0_ENOMEM = 4,      /* workspace smaller than ph0_workspace_bytes() */
     PH0_ETIMEOUT = 5,    /* a bounded device-side wait gave up (the kernel returned cleanly) */
     PH0_ECUDA = 6,       /* a CUDA runtime call failed */
@@ -153,7 +158,10 @@ typedef struct {
     int32_t early_rounds;   /* ph0_barcodes_early_tuned: 1 always sorts the prefix in
                                rounds, 0 never (the whole path); -1 built-in: rounds
                                only for clouds of at least 2^27 edges (n >= 16385)     */
-    int32_t reserved[2];
+    int32_t split_sort;     /* 1: the whole path sorts the edges as two halves merged, as
+                               it always does above 2^32 - 4096 edges (test aid: runs that
+                               form on any n); -1 or 0: only above                       */
+    int32_t reserved;
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits

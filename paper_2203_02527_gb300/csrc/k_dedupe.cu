@@ -48,12 +48,12 @@ k_dedupe(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int
 #pragma unroll
         for (int j = 0; j < IT; ++j) {
             const int i = j * T + tid;
-            kv[j] = i < valid ? keys[base + i] : 0;
+            kv[j] = i < valid ? keys[base + i] & kKeyBits : 0;  // values: bit 63 may carry an index bit
         }
 #pragma unroll
         for (int j = 0; j < IT; ++j) s_key[1 + j * T + tid] = kv[j];
     }
-    if (tid == 0) s_key[0] = base > 0 ? keys[base - 1] : ~keys[0];
+    if (tid == 0) s_key[0] = base > 0 ? keys[base - 1] & kKeyBits : ~keys[0];
     __syncthreads();
 
     // item (row j, warp w, lane) = j*T + w*32 + lane: striped, conflict-free
@@ -163,9 +163,9 @@ k_chunk_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int64_t i = b + q * 32 + lane;
-            k[q] = i < m ? keys[i] : 0;
+            k[q] = i < m ? keys[i] & kKeyBits : 0;  // values: bit 63 may carry an index bit
         }
-        const uint64_t before = b > 0 ? keys[b - 1] : ~k[0];  // lane 0's k[0] is key[0] here
+        const uint64_t before = b > 0 ? keys[b - 1] & kKeyBits : ~k[0];  // lane 0's k[0] is key[0] here
         uint32_t total = 0;
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {

@@ -165,8 +165,10 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     // the record of edge (u, v): key, value, histograms, key range
     auto emit = [&](int u, uint64_t kb) {
         const int64_t e = edge_index(n, u, v);
-        key[e] = kb;
-        val[e] = wide ? uint32_t(e) : (uint32_t(u) << 16) | uint32_t(v);  // wide: the edge index
+        // wide: the value is the edge index, whose bit 32 (above 92,682
+        // points) rides in the key's bit 63, never set by a squared distance
+        key[e] = wide ? kb | (uint64_t(e >> 32) << 63) : kb;
+        val[e] = wide ? uint32_t(e) : (uint32_t(u) << 16) | uint32_t(v);
 #pragma unroll
         for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
         atomicAdd(&s_top[(kb >> kTopShift) & (kMaxRadix - 1)], 1u);

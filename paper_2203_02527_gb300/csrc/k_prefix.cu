@@ -30,7 +30,7 @@ __device__ __forceinline__ PrefixBins prefix_bins(const Header *h) {
 }
 
 __device__ __forceinline__ uint32_t prefix_bin(uint64_t key, const PrefixBins &b) {
-    return uint32_t((key - b.kmin) >> b.shift);  // < kPrefixBins for kmin <= key <= kmax
+    return uint32_t(((key & kKeyBits) - b.kmin) >> b.shift);  // < kPrefixBins for kmin <= key <= kmax
 }
 
 // Step 1: bin counts of all m keys (grid-stride, shared-memory histogram).

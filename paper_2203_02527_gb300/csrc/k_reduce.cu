@@ -166,7 +166,7 @@ __device__ uint32_t tail_rounds(const ReduceArgs &A, Header *h, const uint32_t *
     for (uint32_t i = tid; i < ncur; i += T) {
         const uint32_t p = __ldcg(list + i);
         uint32_t u, v;
-        record_uv(val[p], WIDE, A.n, u, v);
+        rec_uv<WIDE>(val[p], p, A.hib, A.n, u, v);
         s_p[i] = p;
         s_ra[i] = R(find_root(A.parent, __ldcg(A.comp + u)));
         s_rb[i] = R(find_root(A.parent, __ldcg(A.comp + v)));
@@ -357,12 +357,13 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 if (p < wend) {
                     uint32_t vv = vq[qr];
                     // corrupt input: never index past n
-                    const bool bad = WIDE ? int64_t(vv) >= A.m_edges : ((vv >> 16) >= n || (vv & 0xffffu) >= n);
+                    const bool bad = WIDE ? (int64_t(vv) | index_hi(A.hib, p)) >= A.m_edges
+                                          : ((vv >> 16) >= n || (vv & 0xffffu) >= n);
                     if (bad) {  // reported, and never a candidate
                         set_status(h, PH0_EINTERNAL);
                     } else {
                         uint32_t u, v;
-                        record_uv(vv, WIDE, n, u, v);
+                        rec_uv<WIDE>(vv, p, A.hib, n, u, v);
                         if (snap(u) != snap(v)) differ |= 1u << qr;
                     }
                 }
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
                 const int64_t p = b + (int64_t(qr >> 2) * kReduceThreads + tid) * 4 + (qr & 3);
                 if ((differ >> qr) & 1u) {
                     uint32_t u, v;
-                    record_uv(vq[qr], WIDE, n, u, v);
+                    rec_uv<WIDE>(vq[qr], p, A.hib, n, u, v);
                     const uint32_t cu = snap(u), cv = snap(v);
                     const uint32_t lo = cu < cv ? cu : cv, hi = cu < cv ? cv : cu;
                     const PairT pair = (PairT(lo) << (WIDE ? 32 : 16)) | hi;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
             for (int64_t i = gtid; i < ncur; i += gstride) {
                 const uint32_t p = __ldcg(list + i);
                 uint32_t u, v;
-                record_uv(val[p], WIDE, n, u, v);
+                rec_uv<WIDE>(val[p], p, A.hib, n, u, v);
                 const uint32_t ru = find_root(A.parent, __ldcg(A.comp + u));
                 const uint32_t rv = find_root(A.parent, __ldcg(A.comp + v));
                 if (ru == rv) {
@@ -518,6 +519,9 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
         h->candidates = (add ? h->candidates : 0) + candidates;
         h->rounds = (add ? h->rounds : 0) + int64_t(round) + tail_total;
         h->n_bars = __ldcg(&h->npiv);
+        // the scan stopped short of the edges (positions of the reduction stay
+        // below 2^32) without n-1 pivots: not a result
+        if (A.capped && __ldcg(&h->npiv) < target) set_status(h, PH0_ETOOBIG);
         atomicMax(&h->claim_rounds_max, rounds_max);
     }
 }
@@ -530,7 +534,7 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
                        const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                        const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                        const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                       const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n) {
+                       const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, const uint32_t *hib) {
     const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
     const int lane = threadIdx.x & 31;
     if (j >= nb) return;
@@ -554,8 +558,8 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
         for (int q = 0; q < kPer; ++q) {
             const int64_t i = c0 + lane * kPer + q;
             if (i <= int64_t(p)) {
-                const uint64_t k = keys[i];
-                cnt += i == 0 || k != keys[i - 1];
+                const uint64_t k = keys[i] & kKeyBits;
+                cnt += i == 0 || k != (keys[i - 1] & kKeyBits);
             }
         }
         aval = cpref[c0 / kDedupeChunk] + __reduce_add_sync(0xffffffffu, cnt);
@@ -563,8 +567,10 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
     if (lane != 0) return;
     atomicXor(&h->inf_xor, low);
     uint32_t u, v;
-    record_uv(sodd ? val1[p] : val0[p], wide, n, u, v);
-    const uint64_t key = keys[p];
+    const uint32_t vv = sodd ? val1[p] : val0[p];
+    if (wide) edge_uv(int64_t(vv) | index_hi(hib, int64_t(p)), n, u, v);
+    else record_uv(vv, false, n, u, v);
+    const uint64_t key = keys[p] & kKeyBits;
     ph0_bar b;
     b.u = int32_t(u);
     b.v = int32_t(v);
@@ -646,10 +652,11 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s) {
+                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s,
+                        const uint32_t *hib) {
     if (nb <= 0) return cudaSuccess;
     k_emit<<<unsigned((nb + 7) / 8), 256, 0, s>>>(nb, m, h, kk0, kk1, kv0, kv1, kill_h, val0, val1, key0,
-                                                 key1, sort_h, a, cpref, bars, wide, n);
+                                                 key1, sort_h, a, cpref, bars, wide, n, hib);
     return cudaGetLastError();
 }
 

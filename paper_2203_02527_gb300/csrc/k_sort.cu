@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
     uint64_t kmin = ~0ull, kmax = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += int64_t(gridDim.x) * blockDim.x) {
-        const uint64_t k = keys[i];
+        const uint64_t k = keys[i] & kKeyBits;  // bit 63 carries an edge index bit
 #pragma unroll
         for (int p = 0; p < kLowPasses; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & (kRadix - 1)], 1u);
         atomicAdd(&s_top[(k >> kTopShift) & (kMaxRadix - 1)], 1u);
@@ -244,14 +244,14 @@ struct ClassDigit {
 template <int SLOT, int RADIX>
 __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p, const ClassDigit &cd) {
     if constexpr (SLOT == kClassSlot) {
-        const uint32_t bin = uint32_t((key - cd.kmin) >> cd.shift);
+        const uint32_t bin = uint32_t(((key & kKeyBits) - cd.kmin) >> cd.shift);
         uint32_t c = 0;
 #pragma unroll
         for (int q = 1; q < kPrefixClasses; ++q) c += (q < cd.nc && bin >= cd.bound[q]) ? 1u : 0u;
         return c;
     } else {
         if (SLOT < kLowPasses) return uint32_t(key >> (kRadixBits * SLOT)) & (kRadix - 1);
-        const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+        const uint32_t t = uint32_t(((key & kKeyBits) >> kTopShift) - (p.kmin >> kTopShift));
         if (SLOT == kLowPasses && RADIX == kRadix) return cd.lut[t & (kMaxRadix - 1)];
         if (SLOT == kLowPasses) return p.top == 1 ? t : (t & (kRadix - 1));
         return t >> kRadixBits;
@@ -618,7 +618,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
             kout[g] = key;
             vout[g] = INPL ? S.vals_in[i] : S.vals[i];
             if (hist_top) {  // the two top passes' digits: low and high byte of t
-                const uint32_t t = uint32_t((key >> kTopShift) - (plan.kmin >> kTopShift));
+                const uint32_t t = uint32_t(((key & kKeyBits) >> kTopShift) - (plan.kmin >> kTopShift));
                 atomicAdd(&s_next[t & (kRadix - 1)], 1u);
                 atomicAdd(&s_next[kRadix + (t >> kRadixBits)], 1u);
             }
@@ -698,20 +698,21 @@ __device__ int sort_group(uint64_t *keys, uint32_t *vals, int64_t p, int sz, int
     uint32_t vv[kFixCap];
     if (dflag)
         for (int i = 0; i < sz; ++i) dflag[i] = 0;
+    // compared by value (bit 63 of a word carries an edge index bit), moved whole
     bool sorted = true;
     for (int i = 0; i < sz; ++i) {
         kk[i] = keys[p + i];
         vv[i] = vals[p + i];
-        if (i > 0 && kk[i] < kk[i - 1]) sorted = false;
+        if (i > 0 && (kk[i] & kKeyBits) < (kk[i - 1] & kKeyBits)) sorted = false;
     }
     if (sorted) return 0;
     int8_t before[kFixCap];
-    for (int i = 1; i < sz; ++i) before[i] = kk[i] != kk[i - 1];
+    for (int i = 1; i < sz; ++i) before[i] = (kk[i] & kKeyBits) != (kk[i - 1] & kKeyBits);
     for (int i = 1; i < sz; ++i) {  // stable: an equal key stays behind
         const uint64_t k = kk[i];
         const uint32_t v = vv[i];
         int j = i - 1;
-        while (j >= 0 && kk[j] > k) {
+        while (j >= 0 && (kk[j] & kKeyBits) > (k & kKeyBits)) {
             kk[j + 1] = kk[j];
             vv[j + 1] = vv[j];
             --j;
@@ -724,7 +725,7 @@ __device__ int sort_group(uint64_t *keys, uint32_t *vals, int64_t p, int sz, int
         keys[p + i] = kk[i];
         vals[p + i] = vv[i];
         if (i > 0) {
-            const int d = int(kk[i] != kk[i - 1]) - before[i];
+            const int d = int((kk[i] & kKeyBits) != (kk[i - 1] & kKeyBits)) - before[i];
             delta += d;
             if (dflag) dflag[i] = int8_t(d);
         }
@@ -746,7 +747,7 @@ __device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t 
     const uint64_t g = kp >> kShortShift;
     if (start) {
         int sz = 2;  // a group starts here: its size, up to kFixCap + 1
-        while (sz <= kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
+        while (sz <= kFixCap && p + sz < m && ((keys[p + sz] & kKeyBits) >> kShortShift) == g) ++sz;
         if (sz > kFixCap) return false;  // long: its inversions are checked at their own positions
         if (p + sz > chunk_end) {  // reaches into the next chunk: the second kernel sorts it
             defer_list[atomicAdd(defer_count, 1u)] = uint64_t(p);
@@ -759,11 +760,11 @@ __device__ __noinline__ bool fixup_rare(uint64_t *keys, uint32_t *vals, int64_t 
     // start), else the group is out of order
     int64_t st = -1;
     for (int i = 1; i <= kFixCap; ++i)
-        if (p - i < 0 || (keys[p - i] >> kShortShift) != g) {
+        if (p - i < 0 || ((keys[p - i] & kKeyBits) >> kShortShift) != g) {
             st = p - i + 1;
             break;
         }
-    return st < 0 || (st + kFixCap < m && (keys[st + kFixCap] >> kShortShift) == g);
+    return st < 0 || (st + kFixCap < m && ((keys[st + kFixCap] & kKeyBits) >> kShortShift) == g);
 }
 
 // The check of one record at p (its key kp, the previous kq and next kn;
@@ -804,17 +805,17 @@ __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *k
 #pragma unroll
             for (int i = 0; i < kFixPer / 2; ++i) {
                 const ulonglong2 w = src[i];
-                k[2 * i] = w.x;
-                k[2 * i + 1] = w.y;
+                k[2 * i] = w.x & kKeyBits;  // the values (bit 63 may carry an edge index bit)
+                k[2 * i + 1] = w.y & kKeyBits;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < kFixPer; ++i) k[i] = p0 + i < m ? keys[p0 + i] : ~0ull;  // ~0: no key
+            for (int i = 0; i < kFixPer; ++i) k[i] = p0 + i < m ? keys[p0 + i] & kKeyBits : ~0ull;  // ~0: no key
         }
         uint64_t prev = __shfl_up_sync(0xffffffffu, k[kFixPer - 1], 1);
         uint64_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
-        if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] : ~0ull;
-        if (lane == 31) next = b + kFixChunk < m ? keys[b + kFixChunk] : ~0ull;
+        if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] & kKeyBits : ~0ull;
+        if (lane == 31) next = b + kFixChunk < m ? keys[b + kFixChunk] & kKeyBits : ~0ull;
         int count = 0;
 #pragma unroll
         for (int i = 0; i < kFixPer; ++i) {
@@ -844,9 +845,9 @@ __global__ void __launch_bounds__(256) k_sort_fixup_deferred(uint64_t *keys0, ui
     const uint32_t nd = h->defer_count;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += gridDim.x * blockDim.x) {
         const int64_t p = int64_t(defer_list[q]);
-        const uint64_t g = keys[p] >> kShortShift;
+        const uint64_t g = (keys[p] & kKeyBits) >> kShortShift;
         int sz = 1;
-        while (sz < kFixCap && p + sz < m && (keys[p + sz] >> kShortShift) == g) ++sz;
+        while (sz < kFixCap && p + sz < m && ((keys[p + sz] & kKeyBits) >> kShortShift) == g) ++sz;
         int8_t dflag[kFixCap];
         sort_group(keys, vals, p, sz, dflag);  // a zero total may still move counts between chunks
         for (int i = 1; i < sz; ++i)
@@ -1052,6 +1053,106 @@ cudaError_t launch_copy_parity(uint64_t *keys_dst, const uint64_t *keys_src, uin
 cudaError_t launch_copy_if_odd(uint64_t *keys0, const uint64_t *keys1, uint32_t *vals0,
                                const uint32_t *vals1, int64_t m, const Header *h, cudaStream_t s) {
     return launch_copy_parity(keys0, keys1, vals0, vals1, m, h, 1, nullptr, s);
+}
+
+// ---- the merge of two sorted halves (clouds of more than 2^32 edges) ----
+//
+// Above kSplitEdges edges the sort takes the two halves of the edge array
+// (each below 2^32 records) one after the other and merges them: by key
+// value (bit 63 masked), the first half first among equal values (its edge
+// indices, hence (u, v), are the smaller), which is the order of a stable
+// sort of the whole array.  A tile of kMergeTile outputs per CTA: its split
+// points (how many of its first output records come from the first half)
+// come from k_merge_split, its inputs are staged in shared memory, and each
+// thread merges kMergeItems consecutive outputs.
+constexpr int kMergeThreads = 256, kMergeItems = 8, kMergeTile = kMergeThreads * kMergeItems;
+static_assert(kMergeTile % 32 == 0, "tiles cover whole words of the index-bit mask");
+
+// Of the first d records of the merge, how many come from A (A first among
+// equal values).
+template <class KA, class KB>
+__device__ __forceinline__ int64_t merge_split(KA ka, int64_t la, KB kb, int64_t lb, int64_t d) {
+    int64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((ka[mid] & kKeyBits) <= (kb[d - 1 - mid] & kKeyBits)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_merge_split(const uint64_t *ka, int64_t la, const uint64_t *kb, int64_t lb, int64_t *split,
+                              int64_t tiles) {
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t <= tiles; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = t * kMergeTile < la + lb ? t * kMergeTile : la + lb;
+        split[t] = merge_split(ka, la, kb, lb, d);
+    }
+}
+
+// hib: one bit per output record, bit 32 of its edge index (its key's bit
+// 63), or null.
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t *ka, const uint32_t *va, int64_t la,
+                                                         const uint64_t *kb, const uint32_t *vb, int64_t lb,
+                                                         const int64_t *split, uint64_t *ko, uint32_t *vo,
+                                                         uint32_t *hib) {
+    __shared__ uint64_t s_k[kMergeTile];
+    __shared__ uint32_t s_v[kMergeTile];
+    const int64_t total = la + lb, d0 = int64_t(blockIdx.x) * kMergeTile;
+    if (d0 >= total) return;
+    const int64_t d1 = d0 + kMergeTile < total ? d0 + kMergeTile : total;
+    const int64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
+    const int na = int(i1 - i0), nb = int((d1 - i1) - (d0 - i0)), nt = na + nb;
+    const int64_t j0 = d0 - i0;
+    for (int i = threadIdx.x; i < nt; i += kMergeThreads) {
+        const bool fa = i < na;
+        s_k[i] = fa ? ka[i0 + i] : kb[j0 + i - na];
+        s_v[i] = fa ? va[i0 + i] : vb[j0 + i - na];
+    }
+    __syncthreads();
+    const int dd = threadIdx.x * kMergeItems;
+    uint64_t ok[kMergeItems];
+    uint32_t ov[kMergeItems];
+    uint32_t bits = 0;
+    if (dd < nt) {
+        const uint64_t *A = s_k, *B = s_k + na;
+        int i = int(merge_split(A, na, B, nb, dd)), j = dd - i;
+#pragma unroll
+        for (int r = 0; r < kMergeItems; ++r) {
+            if (dd + r >= nt) break;
+            const bool fa = j >= nb || (i < na && (A[i] & kKeyBits) <= (B[j] & kKeyBits));
+            const int src = fa ? i++ : na + j++;
+            ok[r] = s_k[src];
+            ov[r] = s_v[src];
+            bits |= uint32_t(ok[r] >> 63) << r;
+        }
+#pragma unroll
+        for (int r = 0; r < kMergeItems; ++r)
+            if (dd + r < nt) {
+                ko[d0 + dd + r] = ok[r];
+                vo[d0 + dd + r] = ov[r];
+            }
+    }
+    if (hib) {  // four threads' 8 bits make one word (tiles start on whole words)
+        static_assert(kMergeItems == 8, "4 x 8 bits per word");
+        const int lane = threadIdx.x & 31;
+        uint32_t w = bits << (8 * (lane & 3));
+        w |= __shfl_down_sync(0xffffffffu, w, 1);
+        w |= __shfl_down_sync(0xffffffffu, w, 2);
+        if ((lane & 3) == 0 && dd < nt) hib[(d0 + dd) >> 5] = w;
+    }
+}
+
+// Merge (ka, va)[0, la) and (kb, vb)[0, lb), each sorted, into (ko, vo);
+// split: room for (la + lb) / kMergeTile + 2 words.
+cudaError_t launch_merge(const uint64_t *ka, const uint32_t *va, int64_t la, const uint64_t *kb,
+                         const uint32_t *vb, int64_t lb, uint64_t *ko, uint32_t *vo, uint32_t *hib, int64_t *split,
+                         cudaStream_t s) {
+    const int64_t tiles = (la + lb + kMergeTile - 1) / kMergeTile;
+    if (tiles == 0) return cudaSuccess;
+    const int64_t sblocks = (tiles + 1 + 255) / 256;
+    k_merge_split<<<unsigned(sblocks < 65535 ? sblocks : 65535), 256, 0, s>>>(ka, la, kb, lb, split, tiles);
+    k_merge<<<unsigned(tiles), kMergeThreads, 0, s>>>(ka, va, la, kb, vb, lb, split, ko, vo, hib);
+    return cudaGetLastError();
 }
 
 }  // namespace ph0

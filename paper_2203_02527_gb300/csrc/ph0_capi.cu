@@ -30,6 +30,9 @@ cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
 cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
                                 uint32_t *cnt, const int32_t *gate, cudaStream_t s);
 cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s);
+cudaError_t launch_merge(const uint64_t *ka, const uint32_t *va, int64_t la, const uint64_t *kb,
+                         const uint32_t *vb, int64_t lb, uint64_t *ko, uint32_t *vo, uint32_t *hib, int64_t *split,
+                         cudaStream_t s);
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
 // ph0_barcodes_early's built-in choice: rounds from this many edges on
 constexpr int64_t kEarlyMinEdges = int64_t(1) << 27;
@@ -65,7 +68,8 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s);
+                        const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s,
+                        const uint32_t *hib);
 
 namespace {
 
@@ -93,10 +97,13 @@ struct Tune {
     int split16 = kDefaultDistSplit16, tile = -1, top_bits = kDefaultTopBits;
     uint32_t spin_limit = kSpinLimit;
     bool wide = false;  // edge-index records (always above kMaxN points)
+    bool split = false;  // the whole path's sort as two merged halves (always above kSplitEdges edges)
     explicit Tune(const ph0_tuning *t, int64_t n = 0) {
         wide = n > kMaxN;
+        split = n_edges(n) > kSplitEdges;
         if (!t) return;
         if (t->wide_ids == 1) wide = true;
+        if (t->split_sort == 1) split = true;
         if (t->dist_split16 >= 0 && t->dist_split16 <= 16) split16 = t->dist_split16;
         if (t->dist_tile == 32 || t->dist_tile == 64 || t->dist_tile == 128) tile = t->dist_tile;
         if (t->sort_top_bits == 8 || t->sort_top_bits == 9) top_bits = t->sort_top_bits;
@@ -155,12 +162,55 @@ cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, i
     return sort_fallback(ws, L, pts, n, d, ld, t, s);
 }
 
+// Step 2 of the whole path above kSplitEdges edges (or when a test asks for
+// it): the two halves of step 1's records, each below 2^32, sorted one after
+// the other in the main header with the short sort (its fix-up's chunk counts
+// are scratch: step 3 counts again on the merged records) and each with its
+// gated complete sort of the half as it stands (the fix-up permutes only
+// within groups of equal key >> 16, stably, so equal values keep their edge
+// order); both halves end in buffer 1, their merge in buffer 0, with the
+// bitmask of the edge indices' bit 32 above kMaxN points.
+cudaError_t sort_split(void *ws, const Layout &L, const Tune &t, cudaStream_t s) {
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
+    uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
+    const int64_t m = L.m, half = (m / 2) & ~int64_t(3);  // 16-byte aligned rows for both halves
+    const int64_t off[2] = {0, half}, len[2] = {half, m - half};
+    const int32_t *fb = &h->fixup_fallback;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (len[k] <= 0) continue;
+        uint64_t *sk0 = k0 + off[k], *sk1 = k1 + off[k];
+        uint32_t *sv0 = v0 + off[k], *sv1 = v1 + off[k];
+        const int64_t tiles = (len[k] + kSortTile - 1) / kSortTile;
+        e = cudaMemsetAsync(&h->fixup_fallback, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&h->defer_count, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = launch_sort_init(h, look0, tiles, s, t.top_bits, -1, nullptr);
+        if (e == cudaSuccess) e = launch_keystats(sk0, len[k], h, s, nullptr);
+        if (e == cudaSuccess) e = launch_sort_short(sk0, sk1, sv0, sv1, len[k], look0, look1, h, cpref, s);
+        if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, len[k], h, 0, nullptr, s);
+        if (e == cudaSuccess) e = launch_copy_parity(sk0, sk1, sv0, sv1, len[k], h, -1, fb, s);
+        if (e == cudaSuccess) e = launch_sort_init(h, look0, tiles, s, t.top_bits, -1, fb);
+        if (e == cudaSuccess) e = launch_keystats(sk0, len[k], h, s, fb);
+        if (e == cudaSuccess) e = launch_sort_passes(sk0, sk1, sv0, sv1, len[k], look0, look1, h, s, true);
+        if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, len[k], h, 0, fb, s);
+    }
+    uint32_t *hib = L.n > kMaxN ? at<uint32_t>(ws, L.hib) : nullptr;
+    if (e == cudaSuccess)
+        e = launch_merge(k1, v1, len[0], k1 + half, v1 + half, len[1], k0, v0, hib,
+                         reinterpret_cast<int64_t *>(look0), s);  // the sorts' look-back words are free
+    return e;
+}
+
 // Steps 4-5 on the first m sorted edges (m = n(n-1)/2 on the whole path):
 // the pivot claiming.  val is the workspace's ping-pong buffer (sort_h != null
 // selects the one holding the sorted data) or the caller's.
 cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                        const uint32_t *val1, const Header *sort_h, cudaStream_t s,
-                       uint32_t spin_limit = kSpinLimit, bool wide = false, int64_t start = 0) {
+                       uint32_t spin_limit = kSpinLimit, bool wide = false, int64_t start = 0,
+                       const uint32_t *hib = nullptr, bool capped = false) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -184,6 +234,8 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
     A.w0 = w0 < kMaxWindow ? w0 : kMaxWindow;
     A.spin_limit = spin_limit;
     A.start = start;
+    A.hib = hib;
+    A.capped = capped;
     return launch_reduce(A, s);
 }
 
@@ -195,7 +247,8 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
 cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
-                           ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s, bool wide = false) {
+                           ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s, bool wide = false,
+                           const uint32_t *hib = nullptr) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t nb = n - 1;
     if (nb <= 0) return launch_inf(h, n, inf, s);
@@ -214,26 +267,27 @@ cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, cons
     if (e != cudaSuccess) return e;
     e = launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
                     reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
-                    key0, key1, sort_h, a, cpref, bars, wide, n, s);
+                    key0, key1, sort_h, a, cpref, bars, wide, n, s, hib);
     if (e != cudaSuccess) return e;
     return launch_inf(h, n, inf, s);
 }
 
-// Steps 4-5 plus the read-out on all m = n(n-1)/2 sorted edges.
+// Steps 4-5 plus the read-out on the m = n(n-1)/2 sorted edges, or on their
+// first m_scan (the merged sort of more than 2^32 edges, hib its bitmask).
 cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t *val0,
                             const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                             const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
                             ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s,
                             cudaEvent_t after_reduce = nullptr, uint32_t spin_limit = kSpinLimit,
-                            bool wide = false) {
-    const int64_t m = n_edges(n);
-    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit, wide);
+                            bool wide = false, int64_t m_scan = -1, const uint32_t *hib = nullptr) {
+    const int64_t m_all = n_edges(n), m = m_scan >= 0 && m_scan < m_all ? m_scan : m_all;
+    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit, wide, 0, hib, m < m_all);
     if (e != cudaSuccess) return e;
     if (after_reduce) {
         e = cudaEventRecord(after_reduce, s);
         if (e != cudaSuccess) return e;
     }
-    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s, wide);
+    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s, wide, hib);
 }
 
 }  // namespace
@@ -252,7 +306,7 @@ const char *ph0_strerror(int status) {
         case PH0_OK: return "ok";
         case PH0_EINVAL: return "invalid argument";
         case PH0_ENONFINITE: return "non-finite coordinate";
-        case PH0_ETOOBIG: return "size above the supported maximum (n <= 92681, 65535 for the step calls; d <= 1024)";
+        case PH0_ETOOBIG: return "size above the supported maximum (n <= 131071 for ph0_barcodes, 92681 for the other whole-path calls, 65535 for the step calls; d <= 1024), or a cloud whose n-1 killing edges lie beyond the first 2^32 - 4096 sorted edges";
         case PH0_ENOMEM: return "workspace too small";
         case PH0_ETIMEOUT: return "a bounded device-side wait timed out";
         case PH0_ECUDA: return "CUDA runtime error";
@@ -265,7 +319,7 @@ const char *ph0_strerror(int status) {
 int32_t ph0_abi_version(void) { return 4; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
-    if (check_sizes(n, d, d, kMaxNWide) != PH0_OK) return 0;
+    if (check_sizes(n, d, d, kMaxNHuge) != PH0_OK) return 0;
     return Layout(n, d).total;
 }
 
@@ -283,7 +337,7 @@ namespace ph0 {
 int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_bar *bars_dev,
                    ph0_inf_bar *inf_dev, void *ws, size_t ws_bytes, void *stream, const ph0_tuning *tuning,
                    bool fallback) {
-    int rc = check_sizes(n, d, ld, kMaxNWide);
+    int rc = check_sizes(n, d, ld, kMaxNHuge);
     if (rc != PH0_OK) return rc;
     if (!pts_dev || !ws || (n > 1 && !bars_dev)) return PH0_EINVAL;
     if (!aligned(ws, 256) || !aligned(pts_dev, 4) || !aligned(bars_dev, 8) || !aligned(inf_dev, 8))
@@ -298,6 +352,17 @@ int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_b
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
+    if (t.split) {  // two halves merged into buffer 0; positions scanned below 2^32
+        const int64_t mscan = L.m < kMaxScanPos ? L.m : kMaxScanPos;
+        const uint32_t *hib = n > kMaxN ? at<uint32_t>(ws, L.hib) : nullptr;
+        if (e == cudaSuccess) e = sort_split(ws, L, t, s);
+        if (e == cudaSuccess) e = launch_dedupe_count(k0, k0, nullptr, mscan, cpref, nullptr, s);
+        if (e == cudaSuccess) e = launch_dedupe_scan(cpref, mscan, at<uint64_t>(ws, L.dlook), h, s);
+        if (e == cudaSuccess)
+            e = reduce_and_emit(ws, L, n, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, inf_dev, s, nullptr,
+                                t.spin_limit, t.wide, mscan, hib);
+        return cuda_status(e);
+    }
     if (e == cudaSuccess) e = sort_whole(ws, L, pts_dev, n, d, ld, t, s, fallback);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess)

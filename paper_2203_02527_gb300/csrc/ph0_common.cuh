@@ -20,6 +20,17 @@ constexpr int64_t kMaxN = 65535;   // vertex ids packed in 16 bits: E < 2^31
 // count and index a stays below 2^32 while E = n(n-1)/2 < 2^32.
 constexpr int64_t kMaxNWide = 92681;
 static_assert(kMaxNWide * (kMaxNWide - 1) / 2 < (int64_t(1) << 32), "wide edge indices fit 32 bits");
+// Beyond (the whole path only): E < 2^33, so an edge index has 33 bits; its
+// bit 32 rides in bit 63 of the record's key, which a squared distance never
+// sets (it is >= +0), and every reader of a key's value masks it off with
+// kKeyBits.  The sort takes the edges as two halves of fewer than 2^32
+// records each, merged; positions read by the reduction stay below
+// kMaxScanPos (beyond it the call reports PH0_ETOOBIG).
+constexpr int64_t kMaxNHuge = 131071;
+static_assert(kMaxNHuge * (kMaxNHuge - 1) / 2 < (int64_t(1) << 33), "edge indices fit 33 bits");
+constexpr uint64_t kKeyBits = ~(uint64_t(1) << 63);
+constexpr int64_t kSplitEdges = (int64_t(1) << 32) - 4096;  // more edges than this: two halves
+constexpr int64_t kMaxScanPos = (int64_t(1) << 32) - 4096;  // a multiple of the de-duplication chunk
 constexpr int32_t kMaxD = 1024;
 constexpr int kMaxPasses = 8;      // 6 low digit passes + at most 2 top passes
 constexpr int kRadixBits = 8;
@@ -151,6 +162,7 @@ struct Layout {
     size_t kill_key[2], kill_val[2], kill_look[2];
     size_t grad;                         // binary64 gradient accumulator [n, d]
     size_t trace;                        // per-window trace records of the reduction
+    size_t hib;                          // bit 32 of the edge index per sorted record (above kMaxN points)
     size_t total;
 
     __host__ __device__ Layout(int64_t n_, int32_t d_) : n(n_) {
@@ -190,6 +202,7 @@ struct Layout {
         kill_look[1] = take(8 * size_t(ktiles) * kMaxRadix);
         grad = take(8 * size_t(n) * size_t(d_ > 0 ? d_ : 1));
         trace = take(sizeof(uint64_t) * kTraceWords * kTraceWindows);
+        hib = take(n > kMaxN ? 4 * size_t((m + 31) / 32 + 1) : 0);
         total = off;
     }
 };
@@ -278,6 +291,8 @@ struct ReduceArgs {
     int64_t w0;                    // first window size
     int64_t start;                 // first position to scan: 0, or where an earlier launch on the
                                    // same workspace stopped (its state carried, no re-initialization)
+    const uint32_t *hib;           // bit 32 of each record's edge index (records of a merged sort), or null
+    bool capped;                   // m stops short of the edges: fewer than n-1 pivots is PH0_ETOOBIG
     uint64_t *trace;               // [kTraceWindows][kTraceWords]
     uint32_t spin_limit;           // polls before a grid-barrier wait gives up
 };
@@ -357,13 +372,9 @@ __host__ __device__ __forceinline__ int64_t edge_index(int64_t n, int64_t u, int
 // The row u of e is the largest r with r(2n-r-1)/2 <= e: the smaller root of
 // r^2 - (2n-1) r + 2e = 0, estimated in binary32 (off by at most one at
 // n < 2^17) and corrected with exact integer arithmetic.
-__host__ __device__ __forceinline__ void record_uv(uint32_t vv, bool wide, int64_t n, uint32_t &u, uint32_t &v) {
-    if (!wide) {
-        u = vv >> 16;
-        v = vv & 0xffffu;
-        return;
-    }
-    const int64_t e = int64_t(vv), b = 2 * n - 1;
+// (u, v) of the edge with lexicographic index e < n(n-1)/2.
+__host__ __device__ __forceinline__ void edge_uv(int64_t e, int64_t n, uint32_t &u, uint32_t &v) {
+    const int64_t b = 2 * n - 1;
     const int64_t disc = b * b - 8 * e;  // > 0 for e < n(n-1)/2
 #ifdef __CUDA_ARCH__
     const float root = __fsqrt_rn(float(disc));
@@ -378,6 +389,26 @@ __host__ __device__ __forceinline__ void record_uv(uint32_t vv, bool wide, int64
     if (r + 1 <= n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= e) ++r;
     u = uint32_t(r);
     v = uint32_t(e - r * (2 * n - r - 1) / 2 + r + 1);
+}
+__host__ __device__ __forceinline__ void record_uv(uint32_t vv, bool wide, int64_t n, uint32_t &u, uint32_t &v) {
+    if (!wide) {
+        u = vv >> 16;
+        v = vv & 0xffffu;
+        return;
+    }
+    edge_uv(int64_t(vv), n, u, v);
+}
+// Bit 32 of the edge index of the record at position p, from the bitmask the
+// merge of the two sorted halves writes (null: every index below 2^32).
+__host__ __device__ __forceinline__ int64_t index_hi(const uint32_t *hib, int64_t p) {
+    return hib ? int64_t((hib[p >> 5] >> (p & 31)) & 1u) << 32 : 0;
+}
+// (u, v) of the sorted record at position p with value vv.
+template <bool WIDE>
+__device__ __forceinline__ void rec_uv(uint32_t vv, int64_t p, const uint32_t *hib, int64_t n, uint32_t &u,
+                                       uint32_t &v) {
+    if constexpr (WIDE) edge_uv(int64_t(vv) | index_hi(hib, p), n, u, v);
+    else record_uv(vv, false, n, u, v);
 }
 
 // Radix plan.  Bits above the highest bit in which the keys differ are
@@ -431,7 +462,7 @@ constexpr int kDefaultTopBits = 9;
 // Digit of a key in a pass (< 512 in a single top pass, else < 256).
 __host__ __device__ __forceinline__ uint32_t digit_of(uint64_t key, const Plan &p, int pass) {
     if (pass < p.low) return uint32_t(key >> (kRadixBits * pass)) & (kRadix - 1);
-    const uint32_t t = uint32_t((key >> kTopShift) - (p.kmin >> kTopShift));
+    const uint32_t t = uint32_t(((key & kKeyBits) >> kTopShift) - (p.kmin >> kTopShift));
     if (p.top == 1) return t;
     return pass == p.low ? (t & (kRadix - 1)) : (t >> kRadixBits);
 }

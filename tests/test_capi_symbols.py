@@ -75,7 +75,9 @@ def test_bad_input_is_rejected_on_the_host_before_any_cuda_call():
         assert f(pts, 10, 3, 2, bars, inf, ws, need, None) == 1          # ld < d
         assert f(pts, 0, 3, 3, bars, inf, ws, need, None) == 1           # n < 1
         assert f(pts, 10, 0, 3, bars, inf, ws, need, None) == 1          # d < 1
-        assert f(pts, 92682, 3, 3, bars, inf, ws, need, None) == 3       # n > 92681
+        # n above the limit: 131071 for ph0_barcodes (92682 then only outgrows
+        # the workspace), 92681 for the early path
+        assert f(pts, 131072 if name == "ph0_barcodes" else 92682, 3, 3, bars, inf, ws, need, None) == 3
         assert f(pts, 65536, 3, 3, bars, inf, ws, need, None) == 4       # wide records: workspace
         assert f(pts, 10, 1025, 1025, bars, inf, ws, need, None) == 3    # d > 1024
         assert f(None, 10, 3, 3, bars, inf, ws, need, None) == 1         # no points

@@ -160,7 +160,7 @@ def test_invalid_arguments():
     from paper_2203_02527_gb300 import _lib
     lib = _lib.load()
     assert lib.ph0_workspace_bytes(0, 3) == 0
-    assert lib.ph0_workspace_bytes(92682, 3) == 0
+    assert lib.ph0_workspace_bytes(131072, 3) == 0 and lib.ph0_workspace_bytes(131071, 3) > 0
     assert lib.ph0_workspace_bytes(10, 2000) == 0
     ws = torch.empty(lib.ph0_workspace_bytes(10, 3), dtype=torch.uint8, device="cuda")
     pts = torch.from_numpy(inputs.uniform(10, 3, seed=46)).cuda()
@@ -179,7 +179,7 @@ def test_invalid_arguments():
     assert lib.ph0_finish(vp(ws.data_ptr()), None, None) == 0
     assert lib.ph0_barcodes(args[0], 10, 3, 2, *args[4:]) == 1                  # ld < d
     assert lib.ph0_barcodes(args[0], 0, 3, 3, *args[4:]) == 1                   # n < 1
-    assert lib.ph0_barcodes(args[0], 92682, 3, 3, *args[4:]) == 3               # n too big
+    assert lib.ph0_barcodes(args[0], 131072, 3, 3, *args[4:]) == 3              # n too big
     assert lib.ph0_barcodes(*args[:6], args[6], ws.numel() - 1, None) == 4     # small ws
     assert lib.ph0_barcodes(*args[:6], vp(ws.data_ptr() + 8), ws.numel(), None) == 1  # misaligned
     assert lib.ph0_barcodes(*args[:5], vp(inf.data_ptr() + 4), *args[6:]) == 1  # misaligned inf
