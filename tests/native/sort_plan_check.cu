@@ -90,12 +90,13 @@ int main(int argc, char **argv) {
                                  (unsigned long long)kmin, (unsigned long long)kmax, tb);
                 }
             }
-    // raw ranges of every bit width
+    // raw ranges of every bit width, up to the largest key value (63 bits:
+    // bit 63 of a record's key word carries an edge-index bit and is masked)
     for (int w = 0; w <= 63; ++w)
         for (int tb : {8, 9}) {
             const uint64_t kmin = rng() >> 2;
             const uint64_t span = w == 0 ? 0 : (rng() >> (64 - w)) | (1ull << (w - 1));
-            const uint64_t kmax = kmin + span < kmin ? ~0ull : kmin + span;
+            const uint64_t kmax = kmin + span > kKeyBits ? kKeyBits : kmin + span;
             ++cases;
             if (!check(kmin, kmax, tb, rng)) {
                 ++bad;
