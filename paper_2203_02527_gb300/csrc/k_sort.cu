@@ -786,6 +786,9 @@ __device__ __forceinline__ void fixup_at(uint64_t *keys, uint32_t *vals, int64_t
 constexpr int kFixPer = 8;
 constexpr int64_t kFixChunk = 32 * kFixPer;
 static_assert(kFixChunk == kDedupeChunk, "a warp step covers one de-duplication chunk");
+// MASK: the records may carry an edge-index bit in bit 63 of their keys (the
+// halves of the split sort): the streamed keys are masked to their values.
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
                                                      uint32_t *vals1, int64_t m, Header *h, uint32_t *cnt,
                                                      uint64_t *defer_list) {
@@ -795,6 +798,7 @@ __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *k
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    constexpr uint64_t km = MASK ? kKeyBits : ~0ull;
     bool long_unsorted = false;
     for (int64_t b = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kFixChunk; b < m;
          b += nw * kFixChunk) {
@@ -805,17 +809,17 @@ __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *k
 #pragma unroll
             for (int i = 0; i < kFixPer / 2; ++i) {
                 const ulonglong2 w = src[i];
-                k[2 * i] = w.x & kKeyBits;  // the values (bit 63 may carry an edge index bit)
-                k[2 * i + 1] = w.y & kKeyBits;
+                k[2 * i] = w.x & km;
+                k[2 * i + 1] = w.y & km;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < kFixPer; ++i) k[i] = p0 + i < m ? keys[p0 + i] & kKeyBits : ~0ull;  // ~0: no key
+            for (int i = 0; i < kFixPer; ++i) k[i] = p0 + i < m ? keys[p0 + i] & km : ~0ull;  // ~0: no key
         }
         uint64_t prev = __shfl_up_sync(0xffffffffu, k[kFixPer - 1], 1);
         uint64_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
-        if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] & kKeyBits : ~0ull;
-        if (lane == 31) next = b + kFixChunk < m ? keys[b + kFixChunk] & kKeyBits : ~0ull;
+        if (lane == 0) prev = b > 0 && b <= m ? keys[b - 1] & km : ~0ull;
+        if (lane == 31) next = b + kFixChunk < m ? keys[b + kFixChunk] & km : ~0ull;
         int count = 0;
 #pragma unroll
         for (int i = 0; i < kFixPer; ++i) {
@@ -1008,10 +1012,10 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
 // (launch_sort_init), h's histograms complete.  The records end sorted in
 // buffer (passes & 1), unless h->fixup_fallback.
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s);
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s, bool masked);
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool masked) {
     if (m <= 0) return cudaSuccess;
     cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
@@ -1021,18 +1025,21 @@ cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
         if (e != cudaSuccess) return e;
     }
     // the deferred groups' list lives in look1, unused after the passes
-    return launch_sort_fixup(keys0, keys1, vals0, vals1, m, h, cnt, look1, s);
+    return launch_sort_fixup(keys0, keys1, vals0, vals1, m, h, cnt, look1, s, masked);
 }
 
 // The fix-up and its second kernel; cnt: one word per de-duplication chunk;
 // defer_list: room for one word per chunk.
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s) {
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s, bool masked) {
     if (m <= 0) return cudaSuccess;
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = int64_t(sm_count()) * 8;
     if (blocks > cap) blocks = cap;
-    k_sort_fixup<<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);
+    if (masked)
+        k_sort_fixup<true><<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);
+    else
+        k_sort_fixup<false><<<unsigned(blocks), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sort_fixup_deferred<<<unsigned(sm_count()), 256, 0, s>>>(keys0, keys1, vals0, vals1, m, h, cnt, defer_list);

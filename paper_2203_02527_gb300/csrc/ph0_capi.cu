@@ -22,11 +22,12 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
                              int top_bits = kDefaultTopBits, int64_t sorted_edges = -1,
                              const int32_t *gate = nullptr);
+// masked: the records may carry an edge-index bit in bit 63 of their keys (the split sort's halves)
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
-                              cudaStream_t s);
+                              cudaStream_t s, bool masked = false);
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
-                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s);
+                              Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s, bool masked = false);
 cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
                                 uint32_t *cnt, const int32_t *gate, cudaStream_t s);
 cudaError_t launch_dedupe_scan(uint32_t *cpref, int64_t m, uint64_t *look, Header *h, cudaStream_t s);
@@ -189,7 +190,7 @@ cudaError_t sort_split(void *ws, const Layout &L, const Tune &t, cudaStream_t s)
         if (e == cudaSuccess) e = cudaMemsetAsync(&h->defer_count, 0, sizeof(uint32_t), s);
         if (e == cudaSuccess) e = launch_sort_init(h, look0, tiles, s, t.top_bits, -1, nullptr);
         if (e == cudaSuccess) e = launch_keystats(sk0, len[k], h, s, nullptr);
-        if (e == cudaSuccess) e = launch_sort_short(sk0, sk1, sv0, sv1, len[k], look0, look1, h, cpref, s);
+        if (e == cudaSuccess) e = launch_sort_short(sk0, sk1, sv0, sv1, len[k], look0, look1, h, cpref, s, true);
         if (e == cudaSuccess) e = launch_copy_parity(sk1, sk0, sv1, sv0, len[k], h, 0, nullptr, s);
         if (e == cudaSuccess) e = launch_copy_parity(sk0, sk1, sv0, sv1, len[k], h, -1, fb, s);
         if (e == cudaSuccess) e = launch_sort_init(h, look0, tiles, s, t.top_bits, -1, fb);
