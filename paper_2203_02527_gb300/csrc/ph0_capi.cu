@@ -405,11 +405,13 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
         const int r = ph0_barcodes_tuned(pts_dev, n, d, ld, bars_dev, inf_dev, ws, ws_bytes, stream, nullptr);
         return r != PH0_OK ? r : ph0_finish(ws, stream, stats);
     };
-    // the whole path: tiny clouds, wide records, and (built-in choice) clouds
-    // below kEarlyMinEdges, where the rounds' fixed cost exceeds the saving
+    // the whole path: tiny clouds and (built-in choice) clouds below
+    // kEarlyMinEdges, where the rounds' fixed cost exceeds the saving
     const int rounds = tuning ? tuning->early_rounds : -1;
-    if (n < 3 || n > kMaxN || rounds == 0 || (rounds != 1 && L.m < kEarlyMinEdges)) return whole();
-    const Tune t(nullptr);
+    if (n < 3 || rounds == 0 || (rounds != 1 && L.m < kEarlyMinEdges)) return whole();
+    // edge-index records above 65,535 points (or when a test asks for them);
+    // the rounds never split the sort (E < 2^32 up to 92,681 points)
+    const Tune t(tuning, n);
     const int64_t m = L.m;
     Header *h = at<Header>(ws, L.hdr);
     Header *sh = at<Header>(ws, L.aux_hdr);  // header of the segment sorts
@@ -421,7 +423,7 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
 
     // step 1, then the key histogram (read back: the host picks the rounds)
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile);
+    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
     if (e == cudaSuccess) e = launch_prefix_hist(k0, m, h, bins, s);
     std::vector<uint32_t> hb(kPrefixBins);
     if (e == cudaSuccess)
@@ -531,7 +533,7 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
         P = c0 + seg;
         // steps 4-5 on the prefix, resumed where the last round stopped;
         // enough once it holds n-1 pivots
-        e = run_reduce(ws, L, n, P, v0, v0, nullptr, s, kSpinLimit, false, Pprev);
+        e = run_reduce(ws, L, n, P, v0, v0, nullptr, s, kSpinLimit, t.wide, Pprev);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         Header hh;
         if (e == cudaSuccess) e = cudaMemcpy(&hh, h, sizeof(Header), cudaMemcpyDeviceToHost);
@@ -547,7 +549,7 @@ int ph0_barcodes_early_tuned(const float *pts_dev, int64_t n, int32_t d, int64_t
     // step 3 on the prefix (count mode) and the read-out; then the prefix length
     e = launch_dedupe(k0, k0, nullptr, P, nullptr, cpref, dlook, h, s);
     if (e == cudaSuccess)
-        e = order_and_emit(ws, L, n, P, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, inf_dev, s);
+        e = order_and_emit(ws, L, n, P, v0, v0, k0, k0, nullptr, nullptr, cpref, bars_dev, inf_dev, s, t.wide);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h->sorted_edges, &P, sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return PH0_ECUDA;

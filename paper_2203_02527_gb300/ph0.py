@@ -133,7 +133,8 @@ def barcodes(pts: torch.Tensor, ws: Workspace | None = None, stats: bool = False
     return Bars(bars, n, st, inf)
 
 
-def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None, rounds: bool | None = None) -> Bars:
+def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None, rounds: bool | None = None,
+                   tuning: dict | None = None) -> Bars:
     """The same bars as barcodes(), sorting only the prefix of the edge order
     the reduction needs (ph0_barcodes_early_tuned; waits for the GPU).  The
     stats report the prefix length as sorted_edges.  rounds: None lets the
@@ -143,7 +144,7 @@ def barcodes_early(pts: torch.Tensor, ws: Workspace | None = None, rounds: bool 
     ws = ws or _workspace(n, d, pts.device)
     bars = torch.empty((max(n - 1, 0), BAR_BYTES), dtype=torch.uint8, device=pts.device)
     inf = _inf_buffer(pts.device)
-    t = _lib.Tuning.make(early_rounds=-1 if rounds is None else int(bool(rounds)))
+    t = _lib.Tuning.make(**{**(tuning or {}), "early_rounds": -1 if rounds is None else int(bool(rounds))})
     st = Stats()
     check(_lib.load().ph0_barcodes_early_tuned(_ptr(pts), n, d, ld, _ptr(bars), _ptr(inf), ws.ptr, ws.nbytes,
                                                _stream(), ctypes.byref(t), ctypes.byref(st)), "ph0_barcodes_early")

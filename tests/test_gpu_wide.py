@@ -34,6 +34,15 @@ def test_forced_wide_records_match_oracle(case):
     assert got.inf == (inf_v, 0.0, float("inf"))
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_forced_wide_records_in_early_rounds_match_oracle(case):
+    from paper_2203_02527_gb300 import ph0
+    x = CASES[case]()
+    want = oracle.barcodes(x)[0]
+    got = ph0.barcodes_early(torch.from_numpy(np.ascontiguousarray(x)).cuda(), rounds=True, tuning=WIDE)
+    assert_bars_equal(got.numpy(), want)
+
+
 @pytest.mark.parametrize("n", [2, 3, 33, 257, 1000])
 def test_forced_wide_small_and_ragged(n):
     from paper_2203_02527_gb300 import ph0
@@ -55,8 +64,10 @@ def test_largest_cloud_equals_the_prefix_oracle():
     want, kept, _ = oracle.barcodes_below(x, float(bars["death_sq"].max()))
     assert len(want) == n - 1 and kept < 10 ** 8
     assert_bars_equal(bars, want)
-    # the early-terminating entry point takes the whole path here
+    # the early-terminating entry point sorts in rounds here too (a prefix of
+    # the edges; its records hold edge indices as well)
     early = ph0.barcodes_early(torch.from_numpy(x).cuda(), ws=ws)
     assert_bars_equal(early.numpy(), want)
+    assert early.stats["sorted_edges"] < n * (n - 1) // 2 // 10
     del ws, got, early
     torch.cuda.empty_cache()
