@@ -113,6 +113,11 @@ typedef struct {
     int32_t claim_rounds_max;/* most grid-wide claim rounds in one window     */
     int64_t claim_attempts;  /* atomic claims issued in the reduction (two per
                                 candidate column and round)                   */
+    int32_t sort_form;       /* which sort gave the whole path's order: 0 the
+                                short sort of (key, value) records, 1 the packed
+                                sort of 64-bit words, 2 the complete sort run
+                                after a fix-up met a group it cannot order    */
+    int32_t _pad;
 } ph0_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -161,7 +166,12 @@ typedef struct {
     int32_t split_sort;     /* 1: the whole path sorts the edges as two halves merged, as
                                it always does above 2^32 - 4096 edges (test aid: runs that
                                form on any n); -1 or 0: only above                       */
-    int32_t reserved;
+    int32_t packed_sort;    /* the whole path's packed sort (each edge one 64-bit word:
+                               compact top part, key bits 22..47, (u << 15) | v; four
+                               passes; clouds of at most 32768 points whose keys' top
+                               part takes at most 256 values, else the short sort runs;
+                               not with wide_ids = 1): 1 on any such cloud, 0 never,
+                               -1 built-in: from 2^22 edges (n >= 2897) up to n = 32768 */
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits

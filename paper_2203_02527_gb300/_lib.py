@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
         ("n_bars", ctypes.c_int64), ("dist_tiles", ctypes.c_int64),
         ("dist_tiles_int", ctypes.c_int64), ("sorted_edges", ctypes.c_int64),
         ("inf_vertex", ctypes.c_int32), ("claim_rounds_max", ctypes.c_int32),
-        ("claim_attempts", ctypes.c_int64),
+        ("claim_attempts", ctypes.c_int64), ("sort_form", ctypes.c_int32), ("_pad", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -55,15 +55,15 @@ class Tuning(ctypes.Structure):
     _fields_ = [("dist_split16", ctypes.c_int32), ("dist_tile", ctypes.c_int32),
                 ("sort_top_bits", ctypes.c_int32), ("reduce_spin_limit", ctypes.c_int32),
                 ("wide_ids", ctypes.c_int32), ("early_rounds", ctypes.c_int32),
-                ("split_sort", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("split_sort", ctypes.c_int32), ("packed_sort", ctypes.c_int32)]
 
     @classmethod
     def make(cls, dist_split16=-1, dist_tile=-1, sort_top_bits=-1, reduce_spin_limit=-1, wide_ids=-1,
-             early_rounds=-1, split_sort=-1):
+             early_rounds=-1, split_sort=-1, packed_sort=-1):
         t = cls()
         t.dist_split16, t.dist_tile, t.sort_top_bits = dist_split16, dist_tile, sort_top_bits
         t.reduce_spin_limit, t.wide_ids, t.early_rounds = reduce_spin_limit, wide_ids, early_rounds
-        t.split_sort = split_sort
+        t.split_sort, t.packed_sort = split_sort, packed_sort
         return t
 
     def as_dict(self):

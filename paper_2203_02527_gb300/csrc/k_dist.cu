@@ -21,7 +21,8 @@
 // whole tile uses the literal binary64 sequence.
 //
 // Fused: the histograms of the six low 8-bit key digits (the low radix
-// passes) and of the top part of the key modulo 512, the min and max key
+// passes; for the packed sort instead its three key digits, bits 22..47 in
+// 9, 9 and 8 bits) and of the top part of the key modulo 512, the min and max key
 // (the sort's bit range), and the finiteness check of the input.
 #include "emu64.cuh"
 #include "ph0_common.cuh"
@@ -72,7 +73,7 @@ template <int D, int BT>
 __global__ void __launch_bounds__(kDistThreads)
 k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16,
        uint64_t *__restrict__ key, uint32_t *__restrict__ val, Header *__restrict__ h,
-       const int32_t *gate, int wide) {
+       const int32_t *gate, int wide, int packed) {
     if (gate && ld_volatile(gate) == 0) return;  // a gated run (the sort's fallback) that is not needed
     if constexpr (D > 0) {
         d = D;
@@ -81,7 +82,9 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
     // [d][bt] u block, then [d][bt] v block: binary64 values, or int64 fixed
     // point in units of 2^g[k] on the integer path; then g[d], lo[d], hi[d]
     extern __shared__ double s_coord[];
-    __shared__ uint32_t s_hist[kLowPasses][kRadix];
+    __shared__ uint32_t s_hist[kLowPasses][kRadix];  // packed: [3][512] digits of key bits 22..47
+    static_assert(kLowPasses * kRadix == 3 * kMaxRadix, "both histogram sets fit one array");
+    uint32_t *s_flat = &s_hist[0][0];
     __shared__ uint32_t s_top[kMaxRadix];  // (key >> kTopShift) mod kMaxRadix
     __shared__ uint64_t s_min[kDistThreads / 32], s_max[kDistThreads / 32];
     __shared__ int s_fixed;
@@ -169,8 +172,13 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         // points) rides in the key's bit 63, never set by a squared distance
         key[e] = wide ? kb | (uint64_t(e >> 32) << 63) : kb;
         val[e] = wide ? uint32_t(e) : (uint32_t(u) << 16) | uint32_t(v);
+        if (packed) {
 #pragma unroll
-        for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
+            for (int q = 0; q < kPackPasses - 1; ++q) atomicAdd(&s_flat[q * kMaxRadix + pack_key_digit(kb, q)], 1u);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kLowPasses; ++q) atomicAdd(&s_hist[q][(kb >> (8 * q)) & (kRadix - 1)], 1u);
+        }
         atomicAdd(&s_top[(kb >> kTopShift) & (kMaxRadix - 1)], 1u);
         kmin = kb < kmin ? kb : kmin;
         kmax = kb > kmax ? kb : kmax;
@@ -221,8 +229,10 @@ k_dist(const float *__restrict__ pts, int n, int d, int64_t ld, int bt, int hw16
         }
     }
     for (int b = threadIdx.x; b < kLowPasses * kRadix; b += blockDim.x) {
-        const uint32_t c = (&s_hist[0][0])[b];
-        if (c) atomicAdd(&h->hist[b / kRadix][b % kRadix], c);
+        const uint32_t c = s_flat[b];
+        if (!c) continue;
+        if (packed) atomicAdd(&h->phist[b / kMaxRadix][b % kMaxRadix], c);
+        else atomicAdd(&h->hist[b / kRadix][b % kRadix], c);
     }
     for (int b = threadIdx.x; b < kMaxRadix; b += blockDim.x)
         if (s_top[b]) atomicAdd(&h->hist_top_mod[b], s_top[b]);
@@ -243,7 +253,7 @@ int dist_tile(int d, int want) {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
                         uint32_t *val, Header *h, cudaStream_t s, int split16, int tile,
-                        const int32_t *gate, bool wide) {
+                        const int32_t *gate, bool wide, bool packed) {
     if (n < 2) return cudaSuccess;
     const int bt = dist_tile(d, tile);
     const size_t smem = dist_smem(bt, d);
@@ -255,7 +265,7 @@ cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return e;
         kernel<<<unsigned(tiles), kDistThreads, smem, s>>>(pts, int(n), int(d), ld, bt, hw16, key, val, h, gate,
-                                                           wide ? 1 : 0);
+                                                           wide ? 1 : 0, packed ? 1 : 0);
         return cudaGetLastError();
     };
 #define PH0_DIST_CASE(DD)                                       \

@@ -289,6 +289,8 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
     if (m <= 0) return;
     const uint32_t *val = A.val0;
     if (A.sort_h) val = (make_plan(A.sort_h).passes & 1) ? A.val1 : A.val0;
+    // the packed sort's records, unless its fallback replaced them
+    if (A.valp && ld_volatile(&h->packed) != 0 && ld_volatile(&h->fixup_fallback) == 0) val = A.valp;
     const int tid = threadIdx.x;
     const int64_t G = gridDim.x;
     const int64_t gtid = int64_t(blockIdx.x) * kReduceThreads + tid;
@@ -529,15 +531,20 @@ __global__ void __launch_bounds__(kReduceThreads, 1) k_reduce(ReduceArgs A) {
 // One warp per bar: the killing edge, its index a in D, its pivot row, its
 // position, and the death value sqrt(d2) (IEEE round to nearest).  a comes
 // from the caller's per-edge array, or (a == null) from the de-duplication
-// scan's chunk prefix plus the new values of p's chunk up to p.
+// scan's chunk prefix plus the new values of p's chunk up to p.  After the
+// packed sort (pk.recs set, h->packed set, no fallback taken) the record at p
+// is pk.recs[p], the key that of its edge index e in pk.keyidx, and the new
+// values are the bits of pk.flags.
 __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long long *kk0, const unsigned long long *kk1,
                        const uint32_t *kv0, const uint32_t *kv1, const Header *kill_h,
                        const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                        const uint64_t *key1, const Header *sort_h, const uint32_t *a,
-                       const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, const uint32_t *hib) {
+                       const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, const uint32_t *hib,
+                       PackedRecs pk) {
     const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
     const int lane = threadIdx.x & 31;
     if (j >= nb) return;
+    const bool packed = pk.recs && ld_volatile(&h->packed) != 0 && ld_volatile(&h->fixup_fallback) == 0;
     const bool kodd = kill_h && (make_plan(kill_h).passes & 1);
     const bool sodd = sort_h && (make_plan(sort_h).passes & 1);
     const unsigned long long p = kodd ? kk1[j] : kk0[j];
@@ -550,6 +557,12 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
     uint32_t aval;
     if (a) {
         aval = a[p];
+    } else if (packed) {
+        const int64_t c0 = int64_t(p) & ~int64_t(kDedupeChunk - 1);
+        const int64_t wq = (int64_t(p) >> 5) - (c0 >> 5);  // flag words of the chunk before p's
+        uint32_t f = lane <= wq ? pk.flags[(c0 >> 5) + lane] : 0u;  // wq < kDedupeChunk / 32
+        if (lane == wq && (p & 31) != 31) f &= (2u << (p & 31)) - 1u;
+        aval = cpref[c0 / kDedupeChunk] + __reduce_add_sync(0xffffffffu, uint32_t(__popc(f)));
     } else {
         constexpr int kPer = kDedupeChunk / 32;
         const int64_t c0 = int64_t(p) & ~int64_t(kDedupeChunk - 1);
@@ -567,10 +580,20 @@ __global__ void k_emit(int64_t nb, int64_t m, Header *h, const unsigned long lon
     if (lane != 0) return;
     atomicXor(&h->inf_xor, low);
     uint32_t u, v;
-    const uint32_t vv = sodd ? val1[p] : val0[p];
-    if (wide) edge_uv(int64_t(vv) | index_hi(hib, int64_t(p)), n, u, v);
-    else record_uv(vv, false, n, u, v);
-    const uint64_t key = keys[p] & kKeyBits;
+    uint64_t key;
+    if (packed) {
+        record_uv(pk.recs[p], false, n, u, v);
+        if (u >= v || int64_t(v) >= n) {  // only after a reported error
+            set_status(h, PH0_EINTERNAL);
+            return;
+        }
+        key = pk.keyidx[edge_index(n, u, v)] & kKeyBits;
+    } else {
+        const uint32_t vv = sodd ? val1[p] : val0[p];
+        if (wide) edge_uv(int64_t(vv) | index_hi(hib, int64_t(p)), n, u, v);
+        else record_uv(vv, false, n, u, v);
+        key = keys[p] & kKeyBits;
+    }
     ph0_bar b;
     b.u = int32_t(u);
     b.v = int32_t(v);
@@ -653,10 +676,10 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
                         const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s,
-                        const uint32_t *hib) {
+                        const uint32_t *hib, PackedRecs pk) {
     if (nb <= 0) return cudaSuccess;
     k_emit<<<unsigned((nb + 7) / 8), 256, 0, s>>>(nb, m, h, kk0, kk1, kv0, kv1, kill_h, val0, val1, key0,
-                                                 key1, sort_h, a, cpref, bars, wide, n, hib);
+                                                 key1, sort_h, a, cpref, bars, wide, n, hib, pk);
     return cudaGetLastError();
 }
 

@@ -30,39 +30,9 @@
 // agree above bit 16 (k_sort_fixup).  The step entry point and the early
 // path run every pass.  The early path's partition into distance classes is
 // one more pass (slot kClassSlot, digit = class).
-#include "ph0_common.cuh"
+#include "sort_util.cuh"
 
 namespace ph0 {
-
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t &total) {
-    constexpr int NW = THREADS / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < NW ? s_warp[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < NW) s_warp[lane] = wi - w;
-        if (lane == NW - 1) s_warp[NW] = wi;
-    }
-    __syncthreads();
-    total = s_warp[NW];
-    uint32_t r = inc - x + s_warp[warp];
-    __syncthreads();
-    return r;
-}
 
 // Header fields a sort needs zeroed: histograms, key range, tile counters.
 __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int top_bits,
@@ -87,9 +57,11 @@ __global__ void k_sort_init(Header *h, uint64_t *look0, int64_t look_words, int 
 
 // Histograms of the six low digits and the key range of keys not produced by
 // the distance kernel (which computes both itself); gate: return at once
-// unless *gate is set (a fallback sort that is not needed).
+// unless *gate is set (a fallback sort that is not needed).  lows_only: only
+// the six low histograms (a packed-sort call whose keys did not pack, whose
+// distance kernel took the top part's histogram and the key range).
 __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ keys, int64_t m, Header *h,
-                                                   const int32_t *gate) {
+                                                   const int32_t *gate, int lows_only) {
     if (gate && ld_volatile(gate) == 0) return;
     __shared__ uint32_t s_hist[kLowPasses][kRadix];
     __shared__ uint32_t s_top[kMaxRadix];
@@ -118,7 +90,7 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
         s_max[threadIdx.x >> 5] = kmax;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !lows_only) {
         for (int w = 1; w < 8; ++w) {
             kmin = s_min[w] < kmin ? s_min[w] : kmin;
             kmax = s_max[w] > kmax ? s_max[w] : kmax;
@@ -132,6 +104,7 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&h->hist[i / kRadix][i % kRadix], c);
     }
+    if (lows_only) return;
     for (int i = threadIdx.x; i < kMaxRadix; i += blockDim.x)
         if (s_top[i]) atomicAdd(&h->hist_top_mod[i], s_top[i]);
 }
@@ -144,6 +117,7 @@ __global__ void __launch_bounds__(256) k_keystats(const uint64_t *__restrict__ k
 // top part's span occur.
 __global__ void __launch_bounds__(kMaxRadix) k_top_compact(Header *h) {
     __shared__ uint32_t s_warp[kMaxRadix / 32 + 1];
+    if (ld_volatile(&h->packed)) return;  // the packed sort runs instead (k_sortp.cu)
     const int t = threadIdx.x;
     const Plan plan = make_plan(h);
     uint32_t c = 0;
@@ -184,50 +158,6 @@ struct SortSmem {
 static_assert(kMaxRadix <= kSortTile, "top-digit histogram lives in vals_in");
 static_assert(2 * kRadix * 4 <= 8 * kRadix * 2, "in place: the next passes' histogram lives in whist");
 
-// ---- bulk (TMA) copies global -> shared with an mbarrier -------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// global -> shared, 16-byte aligned addresses, size a multiple of 16
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-// Per-thread asynchronous copies global -> shared (the source only needs the
-// alignment of the copy size): a full tile whose rows are not 16-byte aligned.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Bounded wait for phase `parity` of the barrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 // Digit of a key in pass slot SLOT: slots 0..5 are the raw bytes of bits
 // 0..47; slot 6 is the top part (all of it if it has at most 9 bits, else its
 // low byte), or, in the 8-bit instance of slot 6, the number of the top
@@ -258,64 +188,6 @@ __device__ __forceinline__ uint32_t slot_digit(uint64_t key, const Plan &p, cons
     }
 }
 
-// Decoupled look-back for one digit (column `col` of the per-tile status
-// words, stride kMaxRadix): the sum of the counts of all tiles before `tile`
-// (tile 0's PREFIX also holds the digit's global start).  The PREFIX of a
-// recent predecessor is usually close, so kLookWindow predecessors are read
-// at once and folded in order (4 measured fastest on GB300: 8-bit passes
-// 3.6-3.8 ms and the 9-bit top pass 4.7-4.8 ms at 537M keys, against
-// 3.8 and 5.0 ms with 16 and slower still with 2 or 32); waits on
-// unpublished words are bounded.  Counts and prefixes stay below 2^32, so a
-// word's low half is its count and its high half its flag alone, and an
-// unpublished word is all zero.
-#ifndef PH0_LOOK_WINDOW
-#define PH0_LOOK_WINDOW 4
-#endif
-constexpr int kLookWindow = PH0_LOOK_WINDOW;
-__device__ __forceinline__ uint32_t lookback_window(const uint64_t *col, int64_t tile, Header *h) {
-    uint32_t excl = 0;
-    int64_t t = tile - 1;  // next predecessor to fold
-    uint32_t spins = 0;
-    while (t >= 0) {
-        uint32_t lo[kLookWindow], hi[kLookWindow];
-#pragma unroll
-        for (int q = 0; q < kLookWindow; ++q) {
-            const uint64_t w = t - q >= 0 ? ld_volatile(col + (t - q) * kMaxRadix) : 0;
-            lo[q] = uint32_t(w);
-            hi[q] = uint32_t(w >> 32);
-        }
-        // fold AGG words up to the first PREFIX (folded too) or unpublished
-        // word (count 0); past tile 0 nothing is reached, tile 0 being PREFIX
-        bool live = true, done = false;
-        int folded = 0;
-#pragma unroll
-        for (int q = 0; q < kLookWindow; ++q) {
-            if (live) {
-                excl += lo[q];
-                done = hi[q] == kHiPrefix;
-                live = hi[q] == kHiAgg;
-                folded += live;
-            }
-        }
-        if (done) break;
-        t -= folded;
-        if (!live) {  // an unpublished word: wait on it, then take a fresh window
-            bool gave_up = false;
-            while ((ld_volatile(col + t * kMaxRadix) & kFlagMask) == 0) {
-                if (++spins > kSpinLimit || ld_volatile(&h->status) != 0) {
-                    set_status(h, PH0_ETIMEOUT);
-                    gave_up = true;
-                    break;
-                }
-                __nanosleep(spins < 8 ? 32 : 128);
-            }
-            if (gave_up) break;
-        }
-    }
-    return excl;
-}
-
-
 // One radix pass (pass index = SLOT).  Pass p reads buffer p&1 and writes
 // buffer (p+1)&1; its look-back words (kMaxRadix per tile, whatever the
 // pass's radix) live in look[p&1], and it clears its tile's words in
@@ -341,6 +213,7 @@ k_onesweep(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, i
 
     const Plan plan = make_plan(h);
     if (SLOT != kClassSlot && SLOT >= plan.passes) return;
+    if (ld_volatile(&h->packed)) return;  // the packed sort runs instead (k_sortp.cu)
     // slot 6 has two instances, launched one after the other: the 8-bit one
     // works when k_top_compact found at most kRadix top values, the other else
     constexpr bool COMPACT = SLOT == kLowPasses && RADIX == kRadix;
@@ -792,6 +665,7 @@ template <bool MASK>
 __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
                                                      uint32_t *vals1, int64_t m, Header *h, uint32_t *cnt,
                                                      uint64_t *defer_list) {
+    if (ld_volatile(&h->packed)) return;  // the packed sort runs instead (k_sortp.cu)
     const Plan plan = make_plan(h);
     uint64_t *keys = (plan.passes & 1) ? keys1 : keys0;
     uint32_t *vals = (plan.passes & 1) ? vals1 : vals0;
@@ -843,6 +717,7 @@ __global__ void __launch_bounds__(256) k_sort_fixup(uint64_t *keys0, uint64_t *k
 __global__ void __launch_bounds__(256) k_sort_fixup_deferred(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0,
                                                               uint32_t *vals1, int64_t m, const Header *h,
                                                               uint32_t *cnt, const uint64_t *defer_list) {
+    if (ld_volatile(&h->packed)) return;  // the packed sort runs instead (k_sortp.cu)
     const Plan plan = make_plan(h);
     uint64_t *keys = (plan.passes & 1) ? keys1 : keys0;
     uint32_t *vals = (plan.passes & 1) ? vals1 : vals0;
@@ -889,12 +764,13 @@ cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s, const int32_t *gate) {
+cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s, const int32_t *gate,
+                            bool lows_only) {
     if (m <= 0) return cudaSuccess;
     int64_t blocks = (m + 255) / 256;
     const int64_t cap = int64_t(sm_count()) * 8;
     if (blocks > cap) blocks = cap;
-    k_keystats<<<unsigned(blocks), 256, 0, s>>>(keys, m, h, gate);
+    k_keystats<<<unsigned(blocks), 256, 0, s>>>(keys, m, h, gate, lows_only ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1013,15 +889,18 @@ cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0
 // buffer (passes & 1), unless h->fixup_fallback.
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
                               Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s, bool masked);
+// persist_all: every pass on its persistent instance (a short sort that
+// usually returns at once: the packed sort's stand-in).
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
-                              cudaStream_t s, bool masked) {
+                              cudaStream_t s, bool masked, bool persist_all) {
     if (m <= 0) return cudaSuccess;
     cudaError_t e = prepare_sort_kernels();
     if (e != cudaSuccess) return e;
     for (int p = kShortFirstSlot; p < kMaxPasses; ++p) {
         // the last slot works only for keys whose top part needs two passes
-        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s, p == kMaxPasses - 1);
+        e = launch_sort_pass(keys0, keys1, vals0, vals1, m, p, look0, look1, h, s,
+                             persist_all || p == kMaxPasses - 1);
         if (e != cudaSuccess) return e;
     }
     // the deferred groups' list lives in look1, unused after the passes

@@ -18,14 +18,14 @@ namespace ph0 {
 
 cudaError_t launch_dist(const float *pts, int64_t n, int32_t d, int64_t ld, uint64_t *key,
                         uint32_t *val, Header *h, cudaStream_t s, int split16 = -1, int tile = -1,
-                        const int32_t *gate = nullptr, bool wide = false);
+                        const int32_t *gate = nullptr, bool wide = false, bool packed = false);
 cudaError_t launch_sort_init(Header *h, uint64_t *look0, int64_t tiles, cudaStream_t s,
                              int top_bits = kDefaultTopBits, int64_t sorted_edges = -1,
                              const int32_t *gate = nullptr);
 // masked: the records may carry an edge-index bit in bit 63 of their keys (the split sort's halves)
 cudaError_t launch_sort_short(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                               int64_t m, uint64_t *look0, uint64_t *look1, Header *h, uint32_t *cnt,
-                              cudaStream_t s, bool masked = false);
+                              cudaStream_t s, bool masked = false, bool persist_all = false);
 cudaError_t launch_sort_fixup(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1, int64_t m,
                               Header *h, uint32_t *cnt, uint64_t *defer_list, cudaStream_t s, bool masked = false);
 cudaError_t launch_dedupe_count(const uint64_t *keys0, const uint64_t *keys1, const Header *sort_h, int64_t m,
@@ -35,12 +35,22 @@ cudaError_t launch_merge(const uint64_t *ka, const uint32_t *va, int64_t la, con
                          const uint32_t *vb, int64_t lb, uint64_t *ko, uint32_t *vo, uint32_t *hib, int64_t *split,
                          cudaStream_t s);
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
+// The whole path's built-in choice of the packed sort: from this many edges
+// (below, the short sort's fewer launches count for more than its bytes) up
+// to kPackMaxN points.
+constexpr int64_t kPackMinEdges = int64_t(1) << 22;
 // ph0_barcodes_early's built-in choice: rounds from this many edges on
 constexpr int64_t kEarlyMinEdges = int64_t(1) << 27;
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
                                cudaStream_t s);
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s,
-                            const int32_t *gate = nullptr);
+                            const int32_t *gate = nullptr, bool lows_only = false);
+cudaError_t launch_packed_prep(Header *h, cudaStream_t s);
+cudaError_t launch_packed_passes(const uint64_t *keys, const uint32_t *vals, uint64_t *a, uint64_t *b, int64_t m,
+                                 uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s,
+                                 cudaEvent_t *after_pass);
+cudaError_t launch_packed_fixup(const uint64_t *w, int64_t m, int64_t n, const uint64_t *keyidx, uint32_t *recs,
+                                uint32_t *flags, uint32_t *cnt, uint64_t *defer_list, Header *h, cudaStream_t s);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
                                int64_t m, uint64_t *look0, uint64_t *look1, Header *h,
                                cudaStream_t s, bool persist = false);
@@ -70,7 +80,7 @@ cudaError_t launch_emit(int64_t nb, int64_t m, Header *h, const unsigned long lo
                         const uint32_t *val0, const uint32_t *val1, const uint64_t *key0,
                         const uint64_t *key1, const Header *sort_h, const uint32_t *a,
                         const uint32_t *cpref, ph0_bar *bars, bool wide, int64_t n, cudaStream_t s,
-                        const uint32_t *hib);
+                        const uint32_t *hib, PackedRecs pk);
 
 namespace {
 
@@ -99,12 +109,18 @@ struct Tune {
     uint32_t spin_limit = kSpinLimit;
     bool wide = false;  // edge-index records (always above kMaxN points)
     bool split = false;  // the whole path's sort as two merged halves (always above kSplitEdges edges)
+    bool packed = false;  // the whole path's packed sort (k_sortp.cu)
     explicit Tune(const ph0_tuning *t, int64_t n = 0) {
+        const int64_t m = n_edges(n);
         wide = n > kMaxN;
-        split = n_edges(n) > kSplitEdges;
+        split = m > kSplitEdges;
+        packed = m >= kPackMinEdges && n <= kPackMaxN;
         if (!t) return;
         if (t->wide_ids == 1) wide = true;
         if (t->split_sort == 1) split = true;
+        if (t->packed_sort == 0) packed = false;
+        if (t->packed_sort == 1) packed = m >= 1 && n <= kPackMaxN;
+        if (split || wide) packed = false;  // its words take (u, v), not an edge index
         if (t->dist_split16 >= 0 && t->dist_split16 <= 16) split16 = t->dist_split16;
         if (t->dist_tile == 32 || t->dist_tile == 64 || t->dist_tile == 128) tile = t->dist_tile;
         if (t->sort_top_bits == 8 || t->sort_top_bits == 9) top_bits = t->sort_top_bits;
@@ -163,6 +179,47 @@ cudaError_t sort_whole(void *ws, const Layout &L, const float *pts, int64_t n, i
     return sort_fallback(ws, L, pts, n, d, ld, t, s);
 }
 
+// The packed form of step 2 (and of step 3's counts) on the whole path, the
+// keys of step 1 in buffer 0 and its packed histograms in h (k_sortp.cu):
+// the passes and fix-up of the packed sort, then the short sort with its
+// histograms, which runs only when the keys do not pack (h->classic), then
+// the gated complete sort (h->fixup_fallback: a group of the packed sort too
+// long to sort, or a long unsorted group of the short sort).  The packed sort
+// leaves the record (u << 16) | v of each position in the key[1] region and
+// the flags of new values in look[0] (packed_recs); the others leave their
+// records in buffer (passes & 1) of h's plan.  after_pass: kMaxPasses
+// events (those past the fourth pass recorded at once), or null.
+cudaError_t sort_packed(void *ws, const Layout &L, const float *pts, int64_t n, int32_t d, int64_t ld,
+                        const Tune &t, cudaStream_t s, bool fallback, cudaEvent_t *after_pass = nullptr) {
+    if (L.m <= 0) return cudaSuccess;
+    Header *h = at<Header>(ws, L.hdr);
+    uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
+    uint64_t *wb = at<uint64_t>(ws, L.val[0]);  // both value buffers: m words
+    uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
+    uint32_t *cpref = at<uint32_t>(ws, L.cpref);
+    cudaError_t e = launch_packed_prep(h, s);
+    // the words overwrite the values only after pass 0 has read them (into k1)
+    if (e == cudaSuccess)
+        e = launch_packed_passes(k0, at<uint32_t>(ws, L.val[0]), k1, wb, L.m, look0, look1, h, s, after_pass);
+    for (int q = kPackPasses; q < kMaxPasses && after_pass && e == cudaSuccess; ++q)
+        e = cudaEventRecord(after_pass[q], s);  // no such pass
+    // the deferred groups' list lives in look1, unused after the passes
+    if (e == cudaSuccess)
+        e = launch_packed_fixup(wb, L.m, n, k0, at<uint32_t>(ws, L.key[1]), at<uint32_t>(ws, L.look[0]), cpref,
+                                look1, h, s);
+    if (e == cudaSuccess) e = launch_keystats(k0, L.m, h, s, &h->classic, true);
+    if (e == cudaSuccess)
+        e = launch_sort_short(k0, k1, at<uint32_t>(ws, L.val[0]), at<uint32_t>(ws, L.val[1]), L.m, look0, look1, h,
+                              cpref, s, false, true);
+    if (e != cudaSuccess || !fallback) return e;
+    return sort_fallback(ws, L, pts, n, d, ld, t, s);
+}
+
+// What the reduction and the read-out take from the packed sort.
+PackedRecs packed_recs(void *ws, const Layout &L) {
+    return PackedRecs{at<uint32_t>(ws, L.key[1]), at<uint64_t>(ws, L.key[0]), at<uint32_t>(ws, L.look[0])};
+}
+
 // Step 2 of the whole path above kSplitEdges edges (or when a test asks for
 // it): the two halves of step 1's records, each below 2^32, sorted one after
 // the other in the main header with the short sort (its fix-up's chunk counts
@@ -211,7 +268,7 @@ cudaError_t sort_split(void *ws, const Layout &L, const Tune &t, cudaStream_t s)
 cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const uint32_t *val0,
                        const uint32_t *val1, const Header *sort_h, cudaStream_t s,
                        uint32_t spin_limit = kSpinLimit, bool wide = false, int64_t start = 0,
-                       const uint32_t *hib = nullptr, bool capped = false) {
+                       const uint32_t *hib = nullptr, bool capped = false, const uint32_t *valp = nullptr) {
     ReduceArgs A;
     A.n = n;
     A.m = m;
@@ -237,6 +294,7 @@ cudaError_t run_reduce(void *ws, const Layout &L, int64_t n, int64_t m, const ui
     A.start = start;
     A.hib = hib;
     A.capped = capped;
+    A.valp = valp;
     return launch_reduce(A, s);
 }
 
@@ -249,7 +307,7 @@ cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, cons
                            const uint32_t *val1, const uint64_t *key0, const uint64_t *key1,
                            const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
                            ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s, bool wide = false,
-                           const uint32_t *hib = nullptr) {
+                           const uint32_t *hib = nullptr, PackedRecs pk = PackedRecs{}) {
     Header *h = at<Header>(ws, L.hdr);
     const int64_t nb = n - 1;
     if (nb <= 0) return launch_inf(h, n, inf, s);
@@ -268,7 +326,7 @@ cudaError_t order_and_emit(void *ws, const Layout &L, int64_t n, int64_t m, cons
     if (e != cudaSuccess) return e;
     e = launch_emit(nb, m, h, reinterpret_cast<const unsigned long long *>(kk0),
                     reinterpret_cast<const unsigned long long *>(kk1), kv0, kv1, kh, val0, val1,
-                    key0, key1, sort_h, a, cpref, bars, wide, n, s, hib);
+                    key0, key1, sort_h, a, cpref, bars, wide, n, s, hib, pk);
     if (e != cudaSuccess) return e;
     return launch_inf(h, n, inf, s);
 }
@@ -280,15 +338,16 @@ cudaError_t reduce_and_emit(void *ws, const Layout &L, int64_t n, const uint32_t
                             const Header *sort_h, const uint32_t *a, const uint32_t *cpref,
                             ph0_bar *bars, ph0_inf_bar *inf, cudaStream_t s,
                             cudaEvent_t after_reduce = nullptr, uint32_t spin_limit = kSpinLimit,
-                            bool wide = false, int64_t m_scan = -1, const uint32_t *hib = nullptr) {
+                            bool wide = false, int64_t m_scan = -1, const uint32_t *hib = nullptr,
+                            PackedRecs pk = PackedRecs{}) {
     const int64_t m_all = n_edges(n), m = m_scan >= 0 && m_scan < m_all ? m_scan : m_all;
-    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit, wide, 0, hib, m < m_all);
+    cudaError_t e = run_reduce(ws, L, n, m, val0, val1, sort_h, s, spin_limit, wide, 0, hib, m < m_all, pk.recs);
     if (e != cudaSuccess) return e;
     if (after_reduce) {
         e = cudaEventRecord(after_reduce, s);
         if (e != cudaSuccess) return e;
     }
-    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s, wide, hib);
+    return order_and_emit(ws, L, n, m, val0, val1, key0, key1, sort_h, a, cpref, bars, inf, s, wide, hib, pk);
 }
 
 }  // namespace
@@ -317,7 +376,7 @@ const char *ph0_strerror(int status) {
     }
 }
 
-int32_t ph0_abi_version(void) { return 4; }
+int32_t ph0_abi_version(void) { return 5; }
 
 size_t ph0_workspace_bytes(int64_t n, int32_t d) {
     if (check_sizes(n, d, d, kMaxNHuge) != PH0_OK) return 0;
@@ -352,7 +411,16 @@ int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_b
     uint32_t *v0 = at<uint32_t>(ws, L.val[0]), *v1 = at<uint32_t>(ws, L.val[1]);
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = begin_call(ws, L, s, t.top_bits);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
+    if (e == cudaSuccess)
+        e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide, t.packed);
+    if (t.packed) {
+        if (e == cudaSuccess) e = sort_packed(ws, L, pts_dev, n, d, ld, t, s, fallback);
+        if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
+        if (e == cudaSuccess)
+            e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, nullptr,
+                                t.spin_limit, t.wide, -1, nullptr, packed_recs(ws, L));
+        return cuda_status(e);
+    }
     if (t.split) {  // two halves merged into buffer 0; positions scanned below 2^32
         const int64_t mscan = L.m < kMaxScanPos ? L.m : kMaxScanPos;
         const uint32_t *hib = n > kMaxN ? at<uint32_t>(ws, L.hib) : nullptr;
@@ -584,26 +652,34 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     // ev[0] | init, dist | ev[1] | pass p | ev[2+p] ... | fix-up, gated fallback | ev[2+P] |
     // dedupe | ev[3+P] | reduce | ev[4+P] | order pivots, emit | ev[5+P]
     // (P = kMaxPasses; the short sort launches the passes from slot 2 on;
-    // passes that are not needed return at once)
+    // passes that are not needed return at once.  The packed sort: its four
+    // passes, then the fix-up, the short sort that runs only when the keys do
+    // not pack, and the gated fallback)
     const Tune t(tuning, n);
     e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
-    if (e == cudaSuccess) e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide);
+    if (e == cudaSuccess)
+        e = launch_dist(pts_dev, n, d, ld, k0, v0, h, s, t.split16, t.tile, nullptr, t.wide, t.packed);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess && L.m > 0) e = prepare_sort_kernels();
-    for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
-        if (L.m > 0 && p >= kShortSortFirstSlot)  // as launch_sort_short
-            e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s, p == kMaxPasses - 1);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
+    if (t.packed) {
+        if (e == cudaSuccess && L.m > 0) e = sort_packed(ws, L, pts_dev, n, d, ld, t, s, true, ev + 2);
+        for (int p = 0; p < kMaxPasses && e == cudaSuccess && L.m <= 0; ++p) e = cudaEventRecord(ev[2 + p], s);
+    } else {
+        for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
+            if (L.m > 0 && p >= kShortSortFirstSlot)  // as launch_sort_short
+                e = launch_sort_pass(k0, k1, v0, v1, L.m, p, look0, look1, h, s, p == kMaxPasses - 1);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 + p], s);
+        }
+        if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, cpref, look1, s);
+        if (e == cudaSuccess && L.m > 0) e = sort_fallback(ws, L, pts_dev, n, d, ld, t, s);
     }
-    if (e == cudaSuccess && L.m > 0) e = launch_sort_fixup(k0, k1, v0, v1, L.m, h, cpref, look1, s);
-    if (e == cudaSuccess && L.m > 0) e = sort_fallback(ws, L, pts_dev, n, d, ld, t, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + kMaxPasses], s);
     if (e == cudaSuccess) e = launch_dedupe_scan(cpref, L.m, at<uint64_t>(ws, L.dlook), h, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 + kMaxPasses], s);
     if (e == cudaSuccess)
         e = reduce_and_emit(ws, L, n, v0, v1, k0, k1, h, nullptr, cpref, bars_dev, inf_dev, s, ev[4 + kMaxPasses],
-                            t.spin_limit, t.wide);
+                            t.spin_limit, t.wide, -1, nullptr, t.packed ? packed_recs(ws, L) : PackedRecs{});
     if (e == cudaSuccess) e = cudaEventRecord(ev[5 + kMaxPasses], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[5 + kMaxPasses]);
     if (e == cudaSuccess) {
@@ -650,6 +726,8 @@ int ph0_finish(const void *ws, void *stream, ph0_stats *stats) {
         stats->inf_vertex = hh.inf_vertex;
         stats->claim_rounds_max = int32_t(hh.claim_rounds_max);
         stats->claim_attempts = int64_t(hh.claim_attempts);
+        stats->sort_form = hh.fixup_fallback ? 2 : (hh.packed ? 1 : 0);
+        stats->_pad = 0;
     }
     return hh.status;
 }

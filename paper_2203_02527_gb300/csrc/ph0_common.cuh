@@ -39,6 +39,39 @@ constexpr int kLowPasses = 6;      // raw 8-bit digits of key bits 0..47
 constexpr int kTopShift = 48;      // the rest, key >> 48, is sorted offset by kmin >> 48
 constexpr int kMaxRadix = 512;     // one top pass of up to 9 bits
 
+// The packed sort of the whole path (k_sortp.cu), for clouds of at most
+// 32768 points (kPackMaxEdges edges): each edge (u, v) becomes one 64-bit word
+//   [63:56] the number of its key's top part (key >> 48) among the values
+//           that occur (at most 256 of them), [55:30] key bits 22..47,
+//   [29:0]  (u << 15) | v,
+// whose order is the order of (key >> 22, u, v), i.e. of (key >> 22, edge
+// index); four radix passes of 9, 9, 8 and 8 bits (digit q at word bit
+// pack_shift(q)) sort the words, and a fix-up orders each group of equal
+// key >> 22 by the whole key, read from the distance kernel's output (key by
+// edge index).
+constexpr int kPackIdBits = 30;
+constexpr int64_t kPackMaxN = 32768;
+constexpr int64_t kPackMaxEdges = kPackMaxN * (kPackMaxN - 1) / 2;
+constexpr int kPackKeyShift = 22;
+constexpr int kPackKeyBits = 26;   // key bits 22..47
+constexpr int kPackPasses = 4;
+constexpr uint64_t kPackIdMask = (uint64_t(1) << kPackIdBits) - 1;
+__host__ __device__ constexpr int pack_shift(int q) { return q == 0 ? 30 : q == 1 ? 39 : q == 2 ? 48 : 56; }
+__host__ __device__ constexpr int pack_radix(int q) { return q < 2 ? 512 : 256; }
+static_assert(kPackIdBits + kPackKeyBits + 8 == 64 && pack_shift(2) + 8 == pack_shift(3), "word layout");
+// the key's digit that is word digit q < 3 (the distance kernel's histograms)
+__host__ __device__ __forceinline__ uint32_t pack_key_digit(uint64_t key, int q) {
+    return uint32_t(key >> (kPackKeyShift + 9 * q)) & uint32_t(pack_radix(q) - 1);
+}
+// The record (u << 16) | v and the edge index of a word.
+__host__ __device__ __forceinline__ uint32_t pack_record(uint64_t w) {
+    return (uint32_t(w >> 15) & 0x7fffu) << 16 | (uint32_t(w) & 0x7fffu);
+}
+__host__ __device__ __forceinline__ uint32_t pack_edge(uint64_t w, uint32_t n) {
+    const uint32_t u = uint32_t(w >> 15) & 0x7fffu, v = uint32_t(w) & 0x7fffu;
+    return u * (2 * n - u - 1) / 2 + (v - u - 1);  // u(2n-u-1) < 2^31 at n <= 32768
+}
+
 // Bounded device-side waits: about a second at most, then the kernel records
 // PH0_ETIMEOUT in the status word and returns cleanly.
 constexpr uint32_t kSpinLimit = 1u << 24;
@@ -104,11 +137,11 @@ struct Header {
     int32_t top_bits;            // width of a single top radix pass (8 or 9)
     int32_t fixup_fallback;      // set when the short sort's fix-up meets a long unsorted group
     uint32_t defer_count;        // groups the fix-up left to its second kernel
-    uint32_t pad[1];
+    int32_t packed;              // the packed sort runs (set once after step 1; k_sortp.cu)
     int64_t sorted_edges;        // edges sorted: m, or the prefix of the early path
     unsigned long long claim_attempts;  // atomic claims of the reduction (grid and tail rounds)
     uint32_t claim_rounds_max;   // most claim rounds in one window
-    uint32_t pad2;
+    int32_t classic;             // a packed-sort call whose keys do not pack: the short sort runs
     // class partition of the early path (radix slot kClassSlot): the key
     // bins of its histogram and the classes' bin ranges [bound[c], bound[c+1])
     uint64_t part_kmin;
@@ -125,6 +158,10 @@ struct Header {
     int32_t top_compact;
     uint32_t pad3;
     uint8_t top_lut[kMaxRadix];
+    // the packed sort: digit histograms of its four passes (the first three
+    // from the distance kernel, the top one from k_packed_prep) and tile counters
+    uint32_t phist[kPackPasses][kMaxRadix];
+    uint32_t ptile[kPackPasses];
 };
 
 constexpr size_t kHeaderBytes = 32768;
@@ -180,8 +217,10 @@ struct Layout {
         aux_hdr = take(kHeaderBytes);
         key[0] = take(8 * size_t(m));
         key[1] = take(8 * size_t(m));
-        val[0] = take(4 * size_t(m));
-        val[1] = take(4 * size_t(m));
+        // one region for both value buffers: the packed sort uses it as one
+        // buffer of m 8-byte words
+        val[0] = take(8 * size_t(m) + 256);
+        val[1] = val[0] + align_up(4 * size_t(m), 256);
         cpref = take(4 * size_t((m + kDedupeChunk - 1) / kDedupeChunk + 1));
         phist = take(4 * size_t(kPrefixBins));
         look[0] = take(8 * size_t(tiles) * kMaxRadix);
@@ -292,9 +331,21 @@ struct ReduceArgs {
     int64_t start;                 // first position to scan: 0, or where an earlier launch on the
                                    // same workspace stopped (its state carried, no re-initialization)
     const uint32_t *hib;           // bit 32 of each record's edge index (records of a merged sort), or null
+    const uint32_t *valp;          // the packed sort's records, read instead of val0/val1 when
+                                   // h->packed is set and h->fixup_fallback is not; or null
     bool capped;                   // m stops short of the edges: fewer than n-1 pivots is PH0_ETOOBIG
     uint64_t *trace;               // [kTraceWindows][kTraceWords]
     uint32_t spin_limit;           // polls before a grid-barrier wait gives up
+};
+
+// What steps 3-5 read after the packed sort (k_sortp.cu): the record
+// (u << 16) | v at every sorted position, the keys by edge index (the
+// distance kernel's output), and one bit per position marking a new distance
+// value.  Null members: no packed sort.
+struct PackedRecs {
+    const uint32_t *recs;
+    const uint64_t *keyidx;
+    const uint32_t *flags;
 };
 
 // One cloud of a fused small-cloud batch (k_small.cu).

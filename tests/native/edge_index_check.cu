@@ -2,8 +2,10 @@
 // ph0_common.cuh: record_uv), compiled by nvcc for the host only: the
 // decoded (u, v) of every edge index e of an n-point cloud is the edge whose
 // lexicographic index (edge_index) is e.  Exhaustive for n <= 3000, every row
-// start and end (and a stride of the interior) for n up to 92681.  Usage:
-// edge_index_check ; prints "checked failures".
+// start and end (and a stride of the interior) for n up to 92681; for n up
+// to 32768 also the packed sort's edge of a word holding (u << 15) | v
+// (pack_edge, pack_record).  Usage: edge_index_check ; prints
+// "checked failures".
 #include <cstdint>
 #include <cstdio>
 
@@ -21,12 +23,20 @@ static void one(int64_t n, int64_t e) {
         if (bad < 10) std::printf("n=%lld e=%lld -> (%u, %u)\n", (long long)n, (long long)e, u, v);
         ++bad;
     }
+    if (n <= kPackMaxN && u < v && int64_t(v) < n) {
+        const uint64_t w = (uint64_t(0xabcdef) << kPackIdBits) | (uint64_t(u) << 15) | v;
+        ++checked;
+        if (pack_edge(w, uint32_t(n)) != uint32_t(e) || pack_record(w) != ((u << 16) | v)) {
+            if (bad < 10) std::printf("packed n=%lld e=%lld\n", (long long)n, (long long)e);
+            ++bad;
+        }
+    }
 }
 
 int main() {
     for (int64_t n = 2; n <= 3000; n = n < 64 ? n + 1 : n * 5 / 4 + 1)
         for (int64_t e = 0; e < n * (n - 1) / 2; ++e) one(n, e);
-    const int64_t big[] = {65536, 70001, 92680, 92681};
+    const int64_t big[] = {16384, 32767, 32768, 65536, 70001, 92680, 92681};
     for (int64_t n : big) {
         for (int64_t u = 0; u + 1 < n; ++u) {
             const int64_t s = edge_index(n, u, u + 1), t = edge_index(n, u, n - 1);

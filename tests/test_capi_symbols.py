@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     # host-only calls work without a device
     lib2 = _lib.load()
-    assert lib2.ph0_abi_version() == 4
+    assert lib2.ph0_abi_version() == 5
     assert lib2.ph0_strerror(0) == b"ok"
     assert lib2.ph0_workspace_bytes(0, 3) == 0
     assert lib2.ph0_workspace_bytes(256, 3) > 256 * 255 // 2 * 12
