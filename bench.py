@@ -41,6 +41,15 @@ WORKLOAD = "circles32768"
 # the top pass), the fix-up.
 PHASE_TRAFFIC_PER_EDGE = {"k_dist": 10.24, "k_onesweep": 25.31, "k_sort_fixup": 8.18}
 ONESWEEP_TRAFFIC_PER_EDGE = PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
+# The packed sort (clouds up to 32768 points, the benchmark's form): DRAM
+# bytes per edge of the distance kernel, its four passes and its fix-up with
+# the fix-up's second kernel (whose key gathers grow with the share of edges
+# in groups of equal key >> 22), from ncu on the benchmark cloud itself
+# (profiles/launches_packed_circles32768.md); and the algorithmic bytes of
+# each pass: pass 0 reads the key (8 B) and the value (4 B) and writes the
+# word (8 B), the others read and write the word.
+PACKED_TRAFFIC_PER_EDGE = {"k_dist": 11.95, "k_psweep": [22.98, 18.91, 17.94, 17.70], "k_pfixup": 42.29}
+PACKED_PASS_BYTES = [20.0, 16.0, 16.0, 16.0]
 # the algorithmic floor of the phase (steps 1-3): write the records (12 B),
 # read and write them once to sort (24 B), read the keys and write a (12 B)
 PHASE_FLOOR_PER_EDGE = 48.0
@@ -50,6 +59,7 @@ PHASE_FLOOR_PER_EDGE = 48.0
 ADDS_PER_SM_CLK_NOMINAL = 2.0
 ADDS_PER_SM_CLK_MEASURED = 1.6
 METRIC = "edges sorted+reduced/s at N=32768"
+PACKED_PASSES = 4
 # bounded sample of the workload for the CPU oracle: every 5th point
 SAMPLE_STRIDE = 5
 
@@ -286,23 +296,42 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel
     mean = lambda k: float(np.mean([p[k] for p in profs]))  # noqa: E731
     passes = int(st["sort_passes"])
-    # the whole path runs the passes from slot 2 on (the slots below sort key
-    # bits 0..15, which the fix-up completes), so slots 0 and 1 stay empty
+    packed = int(st.get("sort_form", 0)) == 1
+    # the short sort runs the passes from slot 2 on (the slots below sort key
+    # bits 0..15, which the fix-up completes), so slots 0 and 1 stay empty;
+    # the packed sort's four passes take slots 0-3
     pass_ms = [float(np.mean([p["pass_ms"][i] for p in profs])) for i in range(passes)]
     ran = [t for t in pass_ms if t > 0.05]
     stages = {"dist_ms": mean("dist_ms"), "sort_ms": mean("sort_ms"), "pass_ms": pass_ms,
               "fixup_ms": mean("fixup_ms"), "dedupe_ms": mean("dedupe_ms"),
-              "reduce_ms": mean("reduce_ms"), "emit_ms": mean("emit_ms")}
+              "reduce_ms": mean("reduce_ms"), "emit_ms": mean("emit_ms"),
+              "sort_form": "packed" if packed else "short"}
     hbm, hbm_src = peaks()
     per_pass_ms = float(np.mean(ran)) if ran else 0.0
-    # the radix passes: 24 algorithmic bytes per edge per pass, against HBM
-    achieved = 24.0 * m / (per_pass_ms * 1e-3) / 1e9 if per_pass_ms > 0 else 0.0
-    roof_sort = {"kernel": "k_onesweep", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                 "unit": "GB/s", "frac": achieved / hbm,
-                 "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
-                 "traffic_source": "ncu on the 8192-point cloud (slots 4-6), scaled by edges",
-                 "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src,
-                 "launches": len(ran), "ms_per_launch": per_pass_ms}
+    if packed:
+        # the four passes together: their algorithmic bytes over their time
+        alg = sum(PACKED_PASS_BYTES) * m
+        t_all = sum(pass_ms[:PACKED_PASSES]) if len(pass_ms) >= PACKED_PASSES else 0.0
+        achieved = alg / (t_all * 1e-3) / 1e9 if t_all > 0 else 0.0
+        roof_sort = {"kernel": "k_psweep", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": sum(PACKED_TRAFFIC_PER_EDGE["k_psweep"]) * m / PACKED_PASSES,
+                     "traffic_source": "ncu dram bytes of the four passes on the benchmark cloud, per launch",
+                     "algorithmic_bytes": alg / PACKED_PASSES, "peak_source": hbm_src,
+                     "launches": PACKED_PASSES, "ms_per_launch": t_all / PACKED_PASSES,
+                     "per_pass": [{"ms": t, "algorithmic_bytes_per_edge": b,
+                                   "achieved": b * m / (t * 1e-3) / 1e9 if t > 0 else 0.0,
+                                   "frac": b * m / (t * 1e-3) / 1e9 / hbm if t > 0 else 0.0}
+                                  for t, b in zip(pass_ms[:PACKED_PASSES], PACKED_PASS_BYTES)]}
+    else:
+        # the radix passes: 24 algorithmic bytes per edge per pass, against HBM
+        achieved = 24.0 * m / (per_pass_ms * 1e-3) / 1e9 if per_pass_ms > 0 else 0.0
+        roof_sort = {"kernel": "k_onesweep", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": ONESWEEP_TRAFFIC_PER_EDGE * m,
+                     "traffic_source": "ncu on the 8192-point cloud (slots 4-6), scaled by edges",
+                     "algorithmic_bytes": 24.0 * m, "peak_source": hbm_src,
+                     "launches": len(ran), "ms_per_launch": per_pass_ms}
     # the distance kernel: its binding unit is the binary64 adder, which takes
     # the d-1 running-sum additions per edge (the exact squares are formed on
     # the integer ALU); peak = additions per SM per clock x the device's SMs x
@@ -323,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
                                  f"frac_of_probe_rate uses the {ADDS_PER_SM_CLK_MEASURED:g} per SM per clock "
                                  f"a probe measured")}
     # the dominant kernel by time: the radix passes together, or the distances
-    if stages["dist_ms"] >= per_pass_ms * max(len(ran), 1):
+    if stages["dist_ms"] >= sum(ran):
         roof, roof_other = roof_dist, roof_sort
     else:
         roof, roof_other = roof_sort, roof_dist
@@ -331,22 +360,36 @@ def run_ours(args, rank, world, local_rank):
     # of its kernels (ncu, scaled by edges) over its device time, against the
     # copy peak; and the algorithmic floor's bytes over the same time
     phase_ms = stages["dist_ms"] + stages["sort_ms"]
-    phase_bytes = m * (PHASE_TRAFFIC_PER_EDGE["k_dist"] + len(ran) * PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
-                       + PHASE_TRAFFIC_PER_EDGE["k_sort_fixup"])
-    phase = {"kernels": "k_dist, k_onesweep x%d, k_sort_fixup" % len(ran), "ms": phase_ms,
+    if packed:
+        phase_bytes = m * (PACKED_TRAFFIC_PER_EDGE["k_dist"] + sum(PACKED_TRAFFIC_PER_EDGE["k_psweep"])
+                           + PACKED_TRAFFIC_PER_EDGE["k_pfixup"])
+        phase_kernels = "k_dist, k_psweep x4, k_pfixup"
+    else:
+        phase_bytes = m * (PHASE_TRAFFIC_PER_EDGE["k_dist"] + len(ran) * PHASE_TRAFFIC_PER_EDGE["k_onesweep"]
+                           + PHASE_TRAFFIC_PER_EDGE["k_sort_fixup"])
+        phase_kernels = "k_dist, k_onesweep x%d, k_sort_fixup" % len(ran)
+    phase = {"kernels": phase_kernels, "ms": phase_ms,
              "traffic": phase_bytes, "traffic_per_edge": phase_bytes / m,
              "achieved": phase_bytes / (phase_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
              "frac": phase_bytes / (phase_ms * 1e-3) / 1e9 / hbm,
              "floor_per_edge": PHASE_FLOOR_PER_EDGE,
              "floor_frac": PHASE_FLOOR_PER_EDGE * m / (phase_ms * 1e-3) / 1e9 / hbm,
-             "traffic_source": "ncu dram bytes per edge of each kernel on the 8192-point cloud, scaled by edges",
+             "traffic_source": ("ncu dram bytes per edge of each kernel on the benchmark cloud"
+                                if packed else
+                                "ncu dram bytes per edge of each kernel on the 8192-point cloud, scaled by edges"),
              "peak_source": hbm_src}
-    # sort init, distances, radix passes from slot 2, fix-up (and its kernel
-    # for deferred groups), gated fallback (sort init, distances, 8 passes,
-    # de-duplication recount: they return at once unless needed), the
-    # de-duplication scan, reduction (init, kernel), pivot-order sort (sort
-    # init, key stats, 8 passes), emission, the infinite bar
-    launches_per_step = 1 + 1 + 6 + 2 + (1 + 1 + 8 + 1) + 1 + 2 + (1 + 1 + 8) + 1 + 1
+    # sort init, distances, the short sort (passes from slot 2: 8 launches
+    # with slot 6's compaction and its two instances) and its fix-up (and
+    # the kernel for deferred groups), gated fallback (sort init, distances,
+    # 8 pass slots in 10 launches, de-duplication recount: they return at
+    # once unless needed), the de-duplication scan, reduction (init, kernel),
+    # pivot-order sort (sort init, key stats, 10 launches), emission, the
+    # infinite bar; the packed sort adds its check, 4 passes, 2 fix-up
+    # kernels and the short sort's gated key statistics (the short sort's
+    # launches then return at once)
+    launches_per_step = 1 + 1 + (8 + 2) + (1 + 1 + 10 + 1) + 1 + 2 + (1 + 1 + 10) + 1 + 1
+    if packed:
+        launches_per_step += 1 + 4 + 2 + 1
     cpu = cpu_all = cpu_full = None
     if world == 1 and not args.no_cpu_baseline:
         r, dt, ns, ms_ = time_oracle(x)
