@@ -19,8 +19,9 @@
 //
 // A pass moves 16 bytes per edge (an 8-byte word read and written) where the
 // (key, value) records of k_sort.cu move 24, and there are four passes where
-// the short sort runs five.  Pass 0 reads the keys and values in edge order
-// and forms the words as it loads them.
+// the short sort runs five.  Pass 0 reads the keys in edge order and forms
+// the words as it loads them: each thread's items are edges 32 apart, so it
+// finds (u, v) of its first from the edge index and steps along the rows.
 //
 // Gating, on the device: k_packed_prep finds whether the keys pack (their top
 // part spans fewer than 512 values, of which at most 256 occur) and sets
@@ -84,16 +85,15 @@ __device__ __forceinline__ uint32_t pdigit(uint64_t w) {
 #define PH0_PSORT_MIN_BLOCKS 4
 #endif
 
-// Pass Q: reads `in` (pass 0: the keys by edge index, with the values
-// (u << 16) | v in `vin`; else words), writes the words stably ordered by
-// digit Q to `out`.  Its look-back words (kMaxRadix
+// Pass Q: reads `in` (pass 0: the keys by edge index of an n-point cloud;
+// else words), writes the words stably ordered by digit Q to `out`.  Its look-back words (kMaxRadix
 // per tile) live in `look`; it clears its tile's words in `look_next` for the
 // next pass.  One tile of kPTile words per CTA, tiles taken from a counter
 // (every tile a CTA waits on belongs to a CTA already running).
 template <int Q>
 __global__ void __launch_bounds__(kPThreads, PH0_PSORT_MIN_BLOCKS)
-k_psweep(const uint64_t *__restrict__ in, const uint32_t *__restrict__ vin, uint64_t *__restrict__ out, int64_t m,
-         uint64_t *look, uint64_t *look_next, Header *h) {
+k_psweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int64_t m, int32_t n, uint64_t *look,
+         uint64_t *look_next, Header *h) {
     constexpr int R = pack_radix(Q), DPT = R / kPThreads, W = kPThreads / 32, IT = kPItems, TILE = kPTile;
     static_assert(R % kPThreads == 0 && IT * kPThreads == TILE, "tiling");
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -163,15 +163,19 @@ k_psweep(const uint64_t *__restrict__ in, const uint32_t *__restrict__ vin, uint
         }
     }
     if constexpr (Q == 0) {  // form the words: top number, key bits 22..47, (u << 15) | v
+        // (u, v) of the thread's first edge, then of each edge 32 further on:
+        // past the row's end (v = n) the next row begins at v = u + 2
+        uint32_t u = 0, v = 0;
+        const int64_t e0 = base + wloc + lane;
+        if (e0 < m) edge_uv(e0, n, u, v);
 #pragma unroll
         for (int j = 0; j < IT; ++j) {
-            const int loc = wloc + j * 32 + lane;
-            const uint32_t uv = (full || loc < valid) ? vin[base + loc] : 0u;
+            if (j > 0) edge_step(u, v, uint32_t(n), 32);
             const uint64_t key = k[j];
             const uint32_t top = S.lut[(uint32_t(key >> kTopShift) - t0) & (kMaxRadix - 1)];
             k[j] = (uint64_t(top) << 56) |
                    (((key >> kPackKeyShift) & ((uint64_t(1) << kPackKeyBits) - 1)) << kPackIdBits) |
-                   uint64_t(((uv >> 16) << 15) | (uv & 0x7fffu));
+                   uint64_t((u << 15) | (v & 0x7fffu));
         }
     }
     const unsigned lt = (1u << lane) - 1u;
@@ -514,32 +518,33 @@ cudaError_t launch_packed_prep(Header *h, cudaStream_t s) {
 }
 
 template <int Q>
-static cudaError_t launch_psweep(const uint64_t *in, const uint32_t *vin, uint64_t *out, int64_t m, uint64_t *look,
+static cudaError_t launch_psweep(const uint64_t *in, uint64_t *out, int64_t m, int32_t n, uint64_t *look,
                                  uint64_t *look_next, Header *h, cudaStream_t s) {
     constexpr size_t smem = sizeof(PSmem<Q>);
     static_assert(smem <= 48 * 1024, "within the default dynamic shared memory limit (no opt-in)");
     const unsigned tiles = unsigned((m + kPTile - 1) / kPTile);
-    k_psweep<Q><<<tiles, kPThreads, smem, s>>>(in, vin, out, m, look, look_next, h);
+    k_psweep<Q><<<tiles, kPThreads, smem, s>>>(in, out, m, n, look, look_next, h);
     return cudaGetLastError();
 }
 
-// The four passes: keys and values (by edge index) -> a -> b -> a -> b.
-// look0 must be zeroed (launch_sort_init); every buffer 16-byte aligned.
-cudaError_t launch_packed_passes(const uint64_t *keys, const uint32_t *vals, uint64_t *a, uint64_t *b, int64_t m,
-                                 uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s,
-                                 cudaEvent_t *after_pass) {
+// The four passes: keys (by edge index of an n-point cloud) -> a -> b -> a
+// -> b.  look0 must be zeroed (launch_sort_init); every buffer 16-byte aligned.
+cudaError_t launch_packed_passes(const uint64_t *keys, int64_t n, uint64_t *a, uint64_t *b, uint64_t *look0,
+                                 uint64_t *look1, Header *h, cudaStream_t s, cudaEvent_t *after_pass) {
+    const int64_t m = n * (n - 1) / 2;
     if (m <= 0) return cudaSuccess;
-    if (m > kPackMaxEdges) return cudaErrorInvalidValue;
+    if (n > kPackMaxN) return cudaErrorInvalidValue;
     if (((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) &
          15u) != 0)
         return cudaErrorInvalidValue;
-    cudaError_t e = launch_psweep<0>(keys, vals, a, m, look0, look1, h, s);
+    const int32_t nn = int32_t(n);
+    cudaError_t e = launch_psweep<0>(keys, a, m, nn, look0, look1, h, s);
     if (e == cudaSuccess && after_pass) e = cudaEventRecord(after_pass[0], s);
-    if (e == cudaSuccess) e = launch_psweep<1>(a, nullptr, b, m, look1, look0, h, s);
+    if (e == cudaSuccess) e = launch_psweep<1>(a, b, m, nn, look1, look0, h, s);
     if (e == cudaSuccess && after_pass) e = cudaEventRecord(after_pass[1], s);
-    if (e == cudaSuccess) e = launch_psweep<2>(b, nullptr, a, m, look0, look1, h, s);
+    if (e == cudaSuccess) e = launch_psweep<2>(b, a, m, nn, look0, look1, h, s);
     if (e == cudaSuccess && after_pass) e = cudaEventRecord(after_pass[2], s);
-    if (e == cudaSuccess) e = launch_psweep<3>(a, nullptr, b, m, look1, look0, h, s);
+    if (e == cudaSuccess) e = launch_psweep<3>(a, b, m, nn, look1, look0, h, s);
     if (e == cudaSuccess && after_pass) e = cudaEventRecord(after_pass[3], s);
     return e;
 }

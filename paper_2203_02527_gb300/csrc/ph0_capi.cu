@@ -46,9 +46,8 @@ cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h,
 cudaError_t launch_keystats(const uint64_t *keys, int64_t m, Header *h, cudaStream_t s,
                             const int32_t *gate = nullptr, bool lows_only = false);
 cudaError_t launch_packed_prep(Header *h, cudaStream_t s);
-cudaError_t launch_packed_passes(const uint64_t *keys, const uint32_t *vals, uint64_t *a, uint64_t *b, int64_t m,
-                                 uint64_t *look0, uint64_t *look1, Header *h, cudaStream_t s,
-                                 cudaEvent_t *after_pass);
+cudaError_t launch_packed_passes(const uint64_t *keys, int64_t n, uint64_t *a, uint64_t *b, uint64_t *look0,
+                                 uint64_t *look1, Header *h, cudaStream_t s, cudaEvent_t *after_pass);
 cudaError_t launch_packed_fixup(const uint64_t *w, int64_t m, int64_t n, const uint64_t *keyidx, uint32_t *recs,
                                 uint32_t *flags, uint32_t *cnt, uint64_t *defer_list, Header *h, cudaStream_t s);
 cudaError_t launch_sort_passes(uint64_t *keys0, uint64_t *keys1, uint32_t *vals0, uint32_t *vals1,
@@ -198,9 +197,7 @@ cudaError_t sort_packed(void *ws, const Layout &L, const float *pts, int64_t n, 
     uint64_t *look0 = at<uint64_t>(ws, L.look[0]), *look1 = at<uint64_t>(ws, L.look[1]);
     uint32_t *cpref = at<uint32_t>(ws, L.cpref);
     cudaError_t e = launch_packed_prep(h, s);
-    // the words overwrite the values only after pass 0 has read them (into k1)
-    if (e == cudaSuccess)
-        e = launch_packed_passes(k0, at<uint32_t>(ws, L.val[0]), k1, wb, L.m, look0, look1, h, s, after_pass);
+    if (e == cudaSuccess) e = launch_packed_passes(k0, n, k1, wb, look0, look1, h, s, after_pass);
     for (int q = kPackPasses; q < kMaxPasses && after_pass && e == cudaSuccess; ++q)
         e = cudaEventRecord(after_pass[q], s);  // no such pass
     // the deferred groups' list lives in look1, unused after the passes

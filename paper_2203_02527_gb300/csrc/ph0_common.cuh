@@ -63,6 +63,16 @@ static_assert(kPackIdBits + kPackKeyBits + 8 == 64 && pack_shift(2) + 8 == pack_
 __host__ __device__ __forceinline__ uint32_t pack_key_digit(uint64_t key, int q) {
     return uint32_t(key >> (kPackKeyShift + 9 * q)) & uint32_t(pack_radix(q) - 1);
 }
+// (u, v) of the edge k places after edge (u, v) in lexicographic order
+// (while it exists): past the end of row u (v = n) the next row starts at
+// v = u + 2.  Each step of the loop moves to the next row.
+__host__ __device__ __forceinline__ void edge_step(uint32_t &u, uint32_t &v, uint32_t n, uint32_t k) {
+    v += k;
+    while (v >= n && u + 2 < n) {
+        ++u;
+        v = v - n + u + 1;
+    }
+}
 // The record (u << 16) | v and the edge index of a word.
 __host__ __device__ __forceinline__ uint32_t pack_record(uint64_t w) {
     return (uint32_t(w >> 15) & 0x7fffu) << 16 | (uint32_t(w) & 0x7fffu);

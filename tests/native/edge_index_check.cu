@@ -4,7 +4,8 @@
 // lexicographic index (edge_index) is e.  Exhaustive for n <= 3000, every row
 // start and end (and a stride of the interior) for n up to 92681; for n up
 // to 32768 also the packed sort's edge of a word holding (u << 15) | v
-// (pack_edge, pack_record).  Usage: edge_index_check ; prints
+// (pack_edge, pack_record) and the step of its first pass from an edge to
+// the edge 32 places on (edge_step).  Usage: edge_index_check ; prints
 // "checked failures".
 #include <cstdint>
 #include <cstdio>
@@ -29,6 +30,15 @@ static void one(int64_t n, int64_t e) {
         if (pack_edge(w, uint32_t(n)) != uint32_t(e) || pack_record(w) != ((u << 16) | v)) {
             if (bad < 10) std::printf("packed n=%lld e=%lld\n", (long long)n, (long long)e);
             ++bad;
+        }
+        if (e + 32 < n * (n - 1) / 2) {
+            uint32_t su = u, sv = v;
+            edge_step(su, sv, uint32_t(n), 32);
+            ++checked;
+            if (edge_index(n, su, sv) != e + 32 || su >= sv || int64_t(sv) >= n) {
+                if (bad < 10) std::printf("step n=%lld e=%lld -> (%u, %u)\n", (long long)n, (long long)e, su, sv);
+                ++bad;
+            }
         }
     }
 }
