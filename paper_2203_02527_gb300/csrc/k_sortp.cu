@@ -86,10 +86,11 @@ __device__ __forceinline__ uint32_t pdigit(uint64_t w) {
 #endif
 
 // Pass Q: reads `in` (pass 0: the keys by edge index of an n-point cloud;
-// else words), writes the words stably ordered by digit Q to `out`.  Its look-back words (kMaxRadix
-// per tile) live in `look`; it clears its tile's words in `look_next` for the
-// next pass.  One tile of kPTile words per CTA, tiles taken from a counter
-// (every tile a CTA waits on belongs to a CTA already running).
+// else words), writes the words stably ordered by digit Q to `out`.  Its
+// look-back words (kMaxRadix per tile) live in `look`; it clears its tile's
+// words in `look_next` for the next pass.  One tile of kPTile words per CTA,
+// tiles taken from a counter (every tile a CTA waits on belongs to a CTA
+// already running).
 template <int Q>
 __global__ void __launch_bounds__(kPThreads, PH0_PSORT_MIN_BLOCKS)
 k_psweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int64_t m, int32_t n, uint64_t *look,
