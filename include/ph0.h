@@ -171,7 +171,8 @@ typedef struct {
                                passes; clouds of at most 32768 points whose keys' top
                                part takes at most 256 values, else the short sort runs;
                                not with wide_ids = 1): 1 on any such cloud, 0 never,
-                               -1 built-in: from 2^22 edges (n >= 2897) up to n = 32768 */
+                               -1 built-in: from 2^22 edges (n >= 2897) up to n = 32768
+                               in dimension 4 and up                                   */
 } ph0_tuning;
 
 /* Early-terminating whole path (the paper has no counterpart; it exploits

@@ -6,7 +6,10 @@ ph0_barcodes_profiled) and keeps the fastest:
   * dist_split16  -- rows of each 16 of a distance tile that take the running
                      sums on the binary64 units (the rest all in integers),
   * dist_tile     -- points per side of a distance tile (32, 64, 128),
-  * sort_top_bits -- width of the single top radix pass (8 or 9).
+  * sort_top_bits -- width of the single top radix pass (8 or 9),
+  * packed_sort   -- the packed sort (1) or the short sort (0), timed on the
+                     whole path (clouds from 2^22 edges up to 32768 points;
+                     in few dimensions the keys often do not pack).
 Results are cached in a JSON file keyed by GPU name, dimension bucket and
 cloud-size bucket ($PH0_TUNING_CACHE, default ~/.cache/ph0_gb300/tuning.json):
 the best distance tile depends on how many tiles a cloud has to fill the GPU.  No setting
@@ -117,11 +120,16 @@ def tune(d: int, n: int = 8192, repeats: int = 3, seed: int = 7, verbose: bool =
             dist[(split, tile)] = stage_ms(t, "dist_ms")
     (split, tile), _ = min(dist.items(), key=lambda kv: kv[1])
     chosen.update(dist_split16=split, dist_tile=tile)
-    # top radix pass width
-    sort = {bits: stage_ms(dict(chosen, sort_top_bits=bits), "sort_ms") for bits in (8, 9)}
+    # top radix pass width (the short sort's)
+    sort = {bits: stage_ms(dict(chosen, sort_top_bits=bits, packed_sort=0), "sort_ms") for bits in (8, 9)}
     chosen["sort_top_bits"] = min(sort, key=sort.get)
+    # the packed sort against the short sort, on the whole path
+    whole = {}
+    if len(x) * (len(x) - 1) // 2 >= 1 << 22 and len(x) <= 32768:
+        whole = {p: stage_ms(dict(chosen, packed_sort=p), "total_ms") for p in (0, 1)}
+        chosen["packed_sort"] = min(whole, key=whole.get)
     if verbose:
         print({"d": d, "dist_ms": {f"{k[0]}/{k[1]}": v for k, v in dist.items()},
-               "sort_ms": sort, "chosen": chosen})
+               "sort_ms": sort, "whole_ms": whole, "chosen": chosen})
     _store(d, n, chosen)
     return chosen

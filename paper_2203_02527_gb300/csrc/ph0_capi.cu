@@ -37,8 +37,12 @@ cudaError_t launch_merge(const uint64_t *ka, const uint32_t *va, int64_t la, con
 constexpr int kShortSortFirstSlot = 2;  // = kShortFirstSlot of k_sort.cu
 // The whole path's built-in choice of the packed sort: from this many edges
 // (below, the short sort's fewer launches count for more than its bytes) up
-// to kPackMaxN points.
+// to kPackMaxN points, in dimension kPackMinD and up: in fewer dimensions the
+// squared distances of uniform clouds spread over so many binades that more
+// than 256 values of the top part occur (8192 uniform points in 3 dimensions),
+// and the short sort then runs after the packed sort's launches, 14% slower.
 constexpr int64_t kPackMinEdges = int64_t(1) << 22;
+constexpr int32_t kPackMinD = 4;
 // ph0_barcodes_early's built-in choice: rounds from this many edges on
 constexpr int64_t kEarlyMinEdges = int64_t(1) << 27;
 cudaError_t launch_prefix_hist(const uint64_t *keys, int64_t m, const Header *h, uint32_t *bins,
@@ -109,11 +113,11 @@ struct Tune {
     bool wide = false;  // edge-index records (always above kMaxN points)
     bool split = false;  // the whole path's sort as two merged halves (always above kSplitEdges edges)
     bool packed = false;  // the whole path's packed sort (k_sortp.cu)
-    explicit Tune(const ph0_tuning *t, int64_t n = 0) {
+    explicit Tune(const ph0_tuning *t, int64_t n = 0, int32_t d = 0) {
         const int64_t m = n_edges(n);
         wide = n > kMaxN;
         split = m > kSplitEdges;
-        packed = m >= kPackMinEdges && n <= kPackMaxN;
+        packed = m >= kPackMinEdges && n <= kPackMaxN && d >= kPackMinD;
         if (!t) return;
         if (t->wide_ids == 1) wide = true;
         if (t->split_sort == 1) split = true;
@@ -401,7 +405,7 @@ int barcodes_whole(const float *pts_dev, int64_t n, int32_t d, int64_t ld, ph0_b
         return PH0_EINVAL;
     const Layout L(n, d);
     if (ws_bytes < L.total) return PH0_ENOMEM;
-    const Tune t(tuning, n);
+    const Tune t(tuning, n, d);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Header *h = at<Header>(ws, L.hdr);
     uint64_t *k0 = at<uint64_t>(ws, L.key[0]), *k1 = at<uint64_t>(ws, L.key[1]);
@@ -652,7 +656,7 @@ int ph0_barcodes_profiled(const float *pts_dev, int64_t n, int32_t d, int64_t ld
     // passes that are not needed return at once.  The packed sort: its four
     // passes, then the fix-up, the short sort that runs only when the keys do
     // not pack, and the gated fallback)
-    const Tune t(tuning, n);
+    const Tune t(tuning, n, d);
     e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = begin_call(ws, L, s, t.top_bits);
     if (e == cudaSuccess)
