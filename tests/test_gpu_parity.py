@@ -319,4 +319,9 @@ def test_autotuner_picks_valid_settings(tmp_path, monkeypatch):
     t = autotune.tune(3, n=1024, repeats=1)
     assert t["dist_split16"] in (0, 4, 8, 12, 16)
     assert t["dist_tile"] in (64, 128) and t["sort_top_bits"] in (8, 9)
+    assert "packed_sort" not in t  # below 2^22 edges the packed sort is not a candidate
     assert autotune.cached(3, 1024) == t
+    # from 2^22 edges the whole path is timed with both sorts
+    t = autotune.tune(16, n=4096, repeats=1)
+    assert t["packed_sort"] in (0, 1)
+    assert autotune.cached(16, 4096) == t
