@@ -94,7 +94,7 @@ class Options(ctypes.Structure):
 
 H1_DTYPE = np.dtype([
     ("eu", np.int32), ("ev", np.int32), ("tu", np.int32), ("tv", np.int32), ("tw", np.int32),
-    ("birth_a", np.uint32), ("death_a", np.uint32), ("pad", np.int32),
+    ("birth_a", np.uint32), ("death_a", np.uint32), ("_pad", np.int32),
     ("birth_order", np.int64), ("death_order", np.int64), ("death_rank", np.int64),
     ("birth_sq", np.float64), ("death_sq", np.float64),
 ])
