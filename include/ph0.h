@@ -95,7 +95,8 @@ typedef struct {
 /* Counters of the last call on a workspace, read back by ph0_finish(). */
 typedef struct {
     int32_t status;          /* ph0_status of the device-side work            */
-    int32_t sort_passes;     /* radix passes of the key range's plan (the     *
+    int32_t sort_passes;     /* radix passes of the key range's plan (4 for
+                              * the packed sort of sort_form 1; else the     *
                               * whole path runs those from slot 2 on)         */
     int32_t key_bits;        /* varying key bits sorted                       */
     int32_t windows;         /* reduction windows processed                   */
@@ -216,12 +217,15 @@ typedef struct {
     float total_ms;          /* first to last event                          */
     float dist_ms;           /* step 1: distance kernel                       */
     float sort_ms;           /* step 2: all radix passes                      */
-    float pass_ms[8];        /* step 2: each pass (0 for passes not needed)   */
+    float pass_ms[8];        /* step 2: each pass (0 for passes not needed; the
+                                packed sort's four passes in slots 0-3)       */
     float dedupe_ms;         /* step 3                                        */
     float reduce_ms;         /* steps 4-5: pivot claiming                     */
     float emit_ms;           /* ordering of the pivot columns and bar output  */
     float fixup_ms;          /* step 2: the sort's fix-up of the groups its
-                                passes leave (and the fallback, if taken)   */
+                                passes leave (and the fallback, if taken; for
+                                the packed sort also the short sort's gated
+                                launches)                                     */
 } ph0_profile;
 
 /* ph0_barcodes() with a CUDA event between stages; waits for the stream and
