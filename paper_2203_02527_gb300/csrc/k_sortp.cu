@@ -84,6 +84,9 @@ __device__ __forceinline__ uint32_t pdigit(uint64_t w) {
 #ifndef PH0_PSORT_MIN_BLOCKS
 #define PH0_PSORT_MIN_BLOCKS 4
 #endif
+#ifndef PH0_PSORT0_MIN_BLOCKS
+#define PH0_PSORT0_MIN_BLOCKS PH0_PSORT_MIN_BLOCKS
+#endif
 
 // Pass Q: reads `in` (pass 0: the keys by edge index of an n-point cloud;
 // else words), writes the words stably ordered by digit Q to `out`.  Its
@@ -92,7 +95,7 @@ __device__ __forceinline__ uint32_t pdigit(uint64_t w) {
 // tiles taken from a counter (every tile a CTA waits on belongs to a CTA
 // already running).
 template <int Q>
-__global__ void __launch_bounds__(kPThreads, PH0_PSORT_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPThreads, Q == 0 ? PH0_PSORT0_MIN_BLOCKS : PH0_PSORT_MIN_BLOCKS)
 k_psweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int64_t m, int32_t n, uint64_t *look,
          uint64_t *look_next, Header *h) {
     constexpr int R = pack_radix(Q), DPT = R / kPThreads, W = kPThreads / 32, IT = kPItems, TILE = kPTile;
