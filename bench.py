@@ -218,6 +218,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_tune:
         from paper_2203_02527_gb300 import autotune
         tuning = autotune.tune(d, n=n)  # cached for ph0.barcodes below
+    # --sort: the whole path's sort form, else the tuned or built-in choice
+    run_tuning = None
+    if args.sort != "auto":
+        run_tuning = dict(tuning or {}, packed_sort=1 if args.sort == "packed" else 0)
     ws = ph0.Workspace(n, d, dev)
     bars = torch.empty((n - 1, 40), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
@@ -229,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         flush.zero_()
-        ph0.barcodes_profiled(pts, ws, bars)
+        ph0.barcodes_profiled(pts, ws, bars, tuning=run_tuning)
     stats = ph0.finish(ws)
 
     profs = []
@@ -239,7 +243,7 @@ def run_ours(args, rank, world, local_rank):
     with sampler:
         for _ in range(args.steps):
             flush.zero_()  # L2 flush, outside the timed events
-            _, prof = ph0.barcodes_profiled(pts, ws, bars)
+            _, prof = ph0.barcodes_profiled(pts, ws, bars, tuning=run_tuning)
             profs.append(prof)
     barrier()
     wall = time.perf_counter() - wall0
@@ -258,7 +262,7 @@ def run_ours(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         dpts = host_pts.to(dev, non_blocking=True)
-        b = ph0.barcodes(dpts, ws)
+        b = ph0.barcodes(dpts, ws, tuning=run_tuning)
         host_bars = b.raw.to("cpu")
         host_inf = b.inf_raw.to("cpu")  # the bar that never dies
         e1.record()
@@ -435,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "cpu_baseline_allcores": cpu_all,
         "cpu_baseline_full_oracle": cpu_full,
-        "tuning": tuning,
+        "tuning": run_tuning if run_tuning is not None else tuning,
         "serving": serving,
         "descent": descent,
         "h1": h1,
@@ -699,6 +703,9 @@ def main():
     ap.add_argument("--cpu-full-oracle", action="store_true",
                     help="also time the single-threaded oracle on the whole cloud (minutes, ~40 GB of host memory)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
+    ap.add_argument("--sort", choices=["auto", "short", "packed"], default="auto",
+                    help="the whole path's sort: the tuned or built-in choice (auto), the short sort of "
+                         "(key, value) records, or the packed sort of 64-bit words")
     ap.add_argument("--no-early", action="store_true", help="skip timing the early-terminating path")
     ap.add_argument("--no-descent", action="store_true", help="skip the 64-cloud gradient-descent timing")
     ap.add_argument("--no-h1", action="store_true", help="skip the first-homology timing")
