@@ -27,8 +27,10 @@
 //
 // The whole path sorts with the short sort (launch_sort_short): the passes
 // from slot 2 on, then a fix-up of the rare groups of records whose keys
-// agree above bit 16 (k_sort_fixup).  The step entry point and the early
-// path run every pass.  The early path's partition into distance classes is
+// agree above bit 16 (k_sort_fixup); from 2^22 edges up to 32768 points in
+// four or more dimensions it takes the packed sort of k_sortp.cu instead,
+// and the short sort's kernels then return at once unless the keys do not
+// pack.  The step entry point and the early path run every pass.  The early path's partition into distance classes is
 // one more pass (slot kClassSlot, digit = class).
 #include "sort_util.cuh"
 
