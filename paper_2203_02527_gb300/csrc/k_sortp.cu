@@ -288,7 +288,7 @@ k_psweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int64_t m,
 // ---- the fix-up ------------------------------------------------------------
 //
 // A warp takes one de-duplication chunk of kPFixChunk positions at a time,
-// kPFixPer consecutive words per lane.  A position whose word >> 29 differs
+// kPFixPer consecutive words per lane.  A position whose word >> 30 differs
 // from both neighbours' (a singleton: almost every position) is a new
 // distance value.  Each lane fetches the whole keys of its positions that lie
 // in groups (all such loads in flight at once) into shared memory, the lane
@@ -305,6 +305,8 @@ constexpr int64_t kPFixChunk = 32 * kPFixPer;
 constexpr int kPFixWarps = 8;  // warps per CTA
 static_assert(kPFixChunk == kDedupeChunk, "a warp step covers one de-duplication chunk");
 static_assert(kPFixChunk % 32 == 0, "a chunk covers whole flag words");
+static_assert(int64_t(kMaxRadix) * kPFixChunk / kSortTile >= kPFixChunk / (kPFixCap + 1) + 1,
+              "the look-back buffer the list lives in holds every deferred group");
 
 // Sorts sz (key, record) pairs in place by key, stably (an equal key stays
 // behind); returns each member's new-value flag as bit i (member 0's
@@ -334,9 +336,10 @@ __device__ uint32_t sort_pairs_stable(K *kk, R *rr, int sz) {
 #endif
 // w: the sorted words; keyidx: the key of each edge by index; recs: the
 // record (u << 16) | v at each position; flags: bit p = a new distance value
-// at p; cnt: new values per chunk (step 3's count mode); defer_list: one word
-// per chunk.  An edge index >= m (never, when the passes' counts are
-// consistent) is reported.
+// at p; cnt: new values per chunk (step 3's count mode); defer_list: room for
+// kPFixChunk / (kPFixCap + 1) + 1 words per chunk (the long groups that start
+// in it and the group across its end).  A word whose (u, v) is no edge of the
+// cloud (never, when the passes' counts are consistent) is reported.
 __global__ void __launch_bounds__(32 * kPFixWarps, PH0_PFIX_MIN_BLOCKS)
 k_pfixup(const uint64_t *__restrict__ w, int64_t m, int64_t n, const uint64_t *__restrict__ keyidx,
          uint32_t *__restrict__ recs, uint32_t *__restrict__ flags, uint32_t *__restrict__ cnt,
@@ -553,8 +556,9 @@ cudaError_t launch_packed_passes(const uint64_t *keys, int64_t n, uint64_t *a, u
     return e;
 }
 
-// The fix-up and its second kernel (see k_pfixup); defer_list: room for one
-// word per chunk.
+// The fix-up and its second kernel (see k_pfixup); defer_list: room for
+// kPFixChunk / (kPFixCap + 1) + 1 words per chunk (look[1] has kMaxRadix per
+// 4096 edges, 32 per chunk).
 cudaError_t launch_packed_fixup(const uint64_t *w, int64_t m, int64_t n, const uint64_t *keyidx, uint32_t *recs,
                                 uint32_t *flags, uint32_t *cnt, uint64_t *defer_list, Header *h, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
