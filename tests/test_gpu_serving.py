@@ -105,6 +105,39 @@ def test_served_crowded_clouds_run_again_with_the_complete_sort():
             assert done[i].bars.tobytes() == want.astype(done[i].bars.dtype).tobytes()
 
 
+def _crowded_in(n, d, seed):
+    # as _crowded, in d dimensions
+    rng = np.random.default_rng(seed)
+    a = rng.random((n // 2, d)) * 1e-12
+    b = rng.random((n - n // 2, d)) * 1e-12
+    b[:, 1] = 1.0
+    return np.ascontiguousarray(np.concatenate([a, b]), np.float32)
+
+
+def test_served_packed_clouds_equal_plain_and_the_oracle():
+    """Clouds of 2,897 points and more in four or more dimensions take the
+    packed sort, in the context as in plain calls; a crowded one (groups of
+    more than 4096 equal key >> 22) is flagged by the packed fix-up and runs
+    again in full.  Mixed with small clouds, each gives exactly the plain
+    path's bars, and the oracle's."""
+    from paper_2203_02527_gb300 import ph0
+    from paper_2203_02527_gb300.serve import Server, run_stream
+    clouds = [inputs.gaussian_mixture(2900 + 600 * i, (8, 16, 32)[i], k=3, sigma=0.3, seed=990 + i)
+              for i in range(3)]
+    clouds.append(_crowded_in(3000, 8, seed=993))
+    clouds += [inputs.uniform(150 + 37 * i, 3, seed=994 + i) for i in range(6)]
+    forms = [ph0.barcodes(torch.from_numpy(x).cuda()).stats["sort_form"] for x in clouds[:4]]
+    assert forms == [1, 1, 1, 2]
+    with Server(mem_budget=4 << 30, streams=4, small_max_n=180, batch_max=32) as srv:
+        done = run_stream(srv, clouds)
+    for i, x in enumerate(clouds):
+        assert done[i].status == 0
+        _same(done[i].bars, _plain(x))
+    for i in (0, 3):
+        want = oracle.barcodes(clouds[i])[0]
+        assert done[i].bars.tobytes() == want.astype(done[i].bars.dtype).tobytes()
+
+
 def test_serving_errors():
     from paper_2203_02527_gb300._lib import Ph0Error
     from paper_2203_02527_gb300.serve import Server
