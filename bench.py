@@ -185,14 +185,15 @@ def run_reference(args, rank, world):
         rates.append(r)
         secs.append(dt)
     value = float(statistics.mean(rates))
-    sample = (f"every {SAMPLE_STRIDE}th point of the {WORKLOAD} cloud: N={n}, d=16, "
+    workload = WORKLOAD if args.n == 32768 else f"circles{args.n}"
+    sample = (f"every {SAMPLE_STRIDE}th point of the {workload} cloud: N={n}, d=16, "
               f"{m} edges per step, single-threaded oracle (steps 1-5, full reduction)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 32768, "d": 16, "sample": sample},
+        "config": {"workload": workload, "n": args.n, "d": 16, "sample": sample},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
